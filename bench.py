@@ -1,0 +1,281 @@
+"""Throughput of the segmented sieve on GB300: integers sieved per second.
+
+Default workload: count the primes in [0, 10^12) (pi(10^12) = 37607912018)
+in one range, count-only, mod-30 wheel with the pre-sieved pattern.  Prints
+one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbsieve|reference]
+
+With N > 1 (torchrun, one rank per GPU) each rank sieves its own block of
+10^12 integers, [r 10^12, (r + 1) 10^12): independent units, no collective
+on the data path (weak scaling).  --impl reference times the CPU oracle on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+UNITS = 10**12                     # integers per rank per step
+METRIC = "integers sieved/s"
+WORKLOAD = "pi(10^12): count primes in [0, 10^12), one range, count-only, mod-30 wheel + pattern of 7..19"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(target_s: float = 12.0):
+    """The oracle (unchanged) on the host cores, on a bounded sample of the
+    workload: the top of [0, 10^12), sized to about target_s seconds."""
+    import oracle
+    oracle.build()
+    cores = oracle.default_threads()
+    probe = 2 * 10**8
+    t = time.perf_counter()
+    oracle.count(UNITS - probe, UNITS, cores)
+    dt = max(time.perf_counter() - t, 1e-3)
+    n = int(min(UNITS, max(probe, probe * target_s / dt)))
+    n -= n % 30
+    t = time.perf_counter()
+    c = oracle.count(UNITS - n, UNITS, cores)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"count of [10^12 - {n}, 10^12) ({c} primes) on {cores} threads, {dt:.2f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cores = oracle.default_threads()
+    # each step: a bounded slice of the workload, sized to ~1/(K+W) of ~3 minutes
+    per_step_s = max(2.0, 150.0 / (args.steps + args.warmup))
+    probe = 10**8
+    t = time.perf_counter()
+    oracle.count(UNITS - probe, UNITS, cores)
+    dt = max(time.perf_counter() - t, 1e-3)
+    n = int(min(UNITS, max(probe, probe * per_step_s / dt)))
+    n -= n % 30
+    for _ in range(args.warmup):
+        oracle.count(UNITS - n, UNITS, cores)
+    times = []
+    for k in range(args.steps):
+        lo = UNITS - n * (k + 1) if n * (k + 1) <= UNITS else 0
+        t = time.perf_counter()
+        oracle.count(lo, lo + n, cores)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = n * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_integers_per_step": n},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} slices of {n} integers below 10^12"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import paper_1205_4883_gb300 as gb
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    lo, hi = rank * UNITS, (rank + 1) * UNITS
+    sv = gb.Sieve(hi, device=dev)
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 2**20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        sv.count_dev(lo, hi, out)
+    torch.cuda.synchronize()
+    expect = sv.count(lo, hi)
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else str(gpu_id or dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clk:
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (not timed)
+            ev[k][0].record(stream)
+            sv.count_dev(lo, hi, out)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    got = int(out.item())
+    if got != expect:
+        raise RuntimeError(f"count mismatch: {got} != {expect}")
+    ms_step = sum(ms) / len(ms)
+    if ws > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * UNITS / (ms_step * 1e-3)
+
+    # end to end through the C ABI with the host count (the call a user makes)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        c = sv.count(lo, hi)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert c == expect
+
+    peaks, peak_kind = _peaks()
+    clocks = clk.summary()
+    n_sms = props.multi_processor_count
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    clears = sv.crossing_work(lo, hi)
+    peak_ops = n_sms * 32 * sm_max * 1e6  # one shared-memory op per lane per clock
+    achieved = clears / (ms_step * 1e-3)
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lo": lo, "hi": hi, "count": expect,
+                       "segment_bytes": sv.get_param(gb.SIEVE_PARAM_SEGMENT_BYTES),
+                       "threads": sv.get_param(gb.SIEVE_PARAM_THREADS),
+                       "small_limit": sv.get_param(gb.SIEVE_PARAM_SMALL_LIMIT),
+                       "ctas_per_sm": sv.get_param(gb.SIEVE_PARAM_CTAS_PER_SM),
+                       "l2": "flushed between steps (256 MiB write, untimed)",
+                       "parallelism": f"{ws} independent ranges" if ws > 1 else "1 range"},
+            "roofline": {"bound": "alu", "op": "shared-memory bit-clear (atom.shared.and)",
+                         "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                         "frac": achieved / peak_ops, "traffic": None,
+                         "peak_basis": f"{n_sms} SMs x 32 lanes/clk x {sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
+                         "work_per_launch": clears},
+            "clocks": clocks,
+            "e2e": {"value": ws * UNITS / e2e_s, "unit": METRIC, "h2d_bytes_per_step": 72,
+                    "d2h_bytes_per_step": 8},
+            "gpu_launches": args.steps,
+        }
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    sv.close()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbsieve", choices=["gbsieve", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    line = run_gpu(args)
+    ws, rank, _ = _dist()
+    if rank == 0 and line is not None:
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_sample()
+        print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

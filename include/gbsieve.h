@@ -1,0 +1,183 @@
+/*
+ * gbsieve.h -- C ABI of the GB300 segmented sieve of Eratosthenes.
+ *
+ * The operation (paper, Section 3.1, "Algorithm Design"): the sieve of
+ * Eratosthenes marks as composite the multiples of each prime, starting with
+ * the multiples of 2; what stays unmarked is prime.  Section 1 gives the bound
+ * that makes a range sieve possible: n is prime iff no prime <= sqrt(n)
+ * divides it, so [lo, hi) is decided by the "base primes" <= sqrt(hi - 1).
+ * Eq. 3 splits the integers into blocks; here a block is a shared-memory
+ * segment and the last one may be short.
+ *
+ * Conventions shared by every call:
+ *  - Ranges are half-open [lo, hi) of unsigned 64-bit integers, lo <= hi.
+ *    lo == hi is an empty range (0 primes, success).  hi may not exceed the
+ *    context's hi_max (SIEVE_ERANGE), and hi_max is at most 2^62.
+ *  - count(lo, hi) = #{p prime : lo <= p < hi}; 0 and 1 are not prime.
+ *  - Odd-only bitmap: let o0 = lo | 1 (the first odd integer >= lo).  Bit i
+ *    (32-bit word i >> 5, bit i & 31, least significant first, words in
+ *    little-endian order) is 1 iff o0 + 2 i is prime, for
+ *    0 <= i < nbits = ceil((hi - o0) / 2) (0 when o0 >= hi).  The bitmap has
+ *    ceil(nbits / 32) words; bits past nbits in the last word are written 0.
+ *    2 has no bit (it is even); it is counted by count and listed by list.
+ *  - List: the primes of [lo, hi) in ascending order, 2 included.
+ *  - Pointers named *_dev are CUDA device pointers on the context's device,
+ *    owned by the caller (e.g. torch.Tensor.data_ptr()); the library never
+ *    frees them.  All other pointers are host pointers owned by the caller.
+ *  - Every call is synchronous (it returns after the GPU work it started has
+ *    finished) unless its comment says otherwise.  Work runs on the
+ *    context's stream.  A context is not thread-safe; separate contexts are
+ *    independent.
+ *  - Return value: 0 (SIEVE_OK) or a negative SIEVE_E* code; output
+ *    arguments are unspecified on error except where stated.
+ *    sieve_strerror() names a code; sieve_last_error() gives the context's
+ *    last message (e.g. the CUDA error string).
+ */
+#ifndef GBSIEVE_H
+#define GBSIEVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIEVE_OK        0
+#define SIEVE_EINVAL   -1  /* bad argument: lo > hi, NULL pointer, bad size */
+#define SIEVE_ERANGE   -2  /* hi > hi_max, or hi > 2^32 for a uint32 list */
+#define SIEVE_ETRUNC   -3  /* output capacity < result size; *n = size needed */
+#define SIEVE_ENOMEM   -4  /* device or host allocation failed */
+#define SIEVE_ECUDA    -5  /* a CUDA runtime call failed */
+#define SIEVE_ETIMEOUT -6  /* a bounded wait ran out */
+#define SIEVE_EBUSY    -7  /* server: no free slot or memory for the request */
+#define SIEVE_ENOENT   -8  /* server: unknown ticket */
+#define SIEVE_EDEVICE  -9  /* a kernel reported an internal limit was hit */
+
+typedef struct sieve_ctx sieve_ctx;
+
+/*
+ * Create a context for ranges with hi <= hi_max (2 <= hi_max <= 2^62) on CUDA
+ * device `device`.  cuda_stream is a cudaStream_t to run on (NULL: the
+ * context creates and owns its own non-blocking stream).  Creation generates
+ * the base primes <= floor(sqrt(hi_max - 1)) on the device (Section 1's bound)
+ * and the pre-sieved pattern tile; both stay resident until sieve_destroy.
+ * On success *out receives the context.
+ */
+int sieve_create(sieve_ctx **out, uint64_t hi_max, int device, void *cuda_stream);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+void sieve_destroy(sieve_ctx *ctx);
+
+/*
+ * Number of primes in [lo, hi) (Section 3.1 sieve, counted), written to the
+ * host integer *count.
+ */
+int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count);
+
+/*
+ * As sieve_count, but the count is written to the device integer
+ * *count_dev and the call is ASYNCHRONOUS: it returns after enqueueing the
+ * work on the context's stream.  *count_dev is overwritten.
+ */
+int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_dev);
+
+/*
+ * Odd-only prime bitmap of [lo, hi) (layout above) into out_dev[0 .. words),
+ * words = ceil(nbits / 32).  out_words is the capacity of out_dev in 32-bit
+ * words: fewer than needed gives SIEVE_ETRUNC and writes nothing.  Words
+ * past the needed ones are not touched.  If count is not NULL the number of
+ * primes in [lo, hi) is also written to the host integer *count.
+ */
+int sieve_bitmap(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev,
+                 size_t out_words, uint64_t *count);
+
+/* Number of 32-bit words of the odd-only bitmap of [lo, hi). */
+uint64_t sieve_bitmap_words(uint64_t lo, uint64_t hi);
+
+/*
+ * Ascending list of the primes in [lo, hi) as uint32 values into
+ * out_dev[0 .. *n).  Requires hi <= 2^32 (SIEVE_ERANGE otherwise).  *n
+ * receives the number of primes in the range even when it exceeds cap; then
+ * the call returns SIEVE_ETRUNC and writes nothing, so out_dev = NULL with
+ * cap = 0 is the size query.  Uses a context-owned scratch bitmap that grows
+ * to the largest range listed so far.
+ */
+int sieve_list(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev,
+               size_t cap, uint64_t *n);
+
+/* As sieve_list with uint64 values; any hi <= hi_max. */
+int sieve_list64(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out_dev,
+                 size_t cap, uint64_t *n);
+
+/*
+ * Compaction only: the ascending uint32 prime list of [lo, hi) read from an
+ * odd-only bitmap of [lo, hi) that is already on the device (bitmap_dev,
+ * layout above, e.g. written by sieve_bitmap).  Same *n / cap / ETRUNC
+ * contract as sieve_list; requires hi <= 2^32.
+ */
+int sieve_compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo,
+                  uint64_t hi, uint32_t *out_dev, size_t cap, uint64_t *n);
+
+/*
+ * Batched counting: m ranges [lo[i], hi[i]) (host arrays) sieved by one
+ * persistent kernel launch (replayed from a CUDA graph captured per batch
+ * capacity).  counts[i] (host) receives each range's prime count.  If
+ * bitmaps_dev is not NULL, bitmaps_dev[i] (a host array of device pointers,
+ * any of which may be NULL) receives range i's odd-only bitmap; its capacity
+ * must be at least sieve_bitmap_words(lo[i], hi[i]) words.  m = 0 is a no-op.
+ */
+int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi,
+                      size_t m, uint64_t *counts, uint32_t *const *bitmaps_dev);
+
+/* Tunable launch parameters (see sieve_set_param / sieve_get_param). */
+#define SIEVE_PARAM_SEGMENT_BYTES 1 /* shared-memory segment, bytes; multiple of 32 */
+#define SIEVE_PARAM_THREADS       2 /* threads per CTA: 256, 512 or 1024 */
+#define SIEVE_PARAM_SMALL_LIMIT   3 /* primes below this are crossed warp-cooperatively */
+#define SIEVE_PARAM_CTAS_PER_SM   4 /* persistent CTAs per SM */
+
+/* Set a launch parameter for later calls on ctx (SIEVE_EINVAL if out of range). */
+int sieve_set_param(sieve_ctx *ctx, int param, int64_t value);
+/* Read a launch parameter into *value. */
+int sieve_get_param(sieve_ctx *ctx, int param, int64_t *value);
+
+/* Facts about the context: base prime count and limit, SM count. */
+typedef struct {
+    uint64_t hi_max;
+    uint64_t prime_limit;   /* floor(sqrt(hi_max - 1)) */
+    uint64_t n_base_primes; /* primes <= prime_limit, 2 included */
+    int32_t device;
+    int32_t num_sms;
+    uint64_t device_bytes;  /* device memory the context holds */
+} sieve_info;
+
+int sieve_get_info(sieve_ctx *ctx, sieve_info *info);
+
+/*
+ * Copy the context's resident base primes (ascending uint32, 2 first) to the
+ * host array out[0 .. min(cap, n)); *n receives their number.
+ */
+int sieve_base_primes(sieve_ctx *ctx, uint32_t *out, size_t cap, uint64_t *n);
+
+/*
+ * Exact number of bit-clears the crossing-off loop performs for [lo, hi):
+ * the multiples p*m in [lo, hi) with p a base prime >= 23, m >= p and m
+ * coprime to 30 (the mod-30 wheel after the pre-sieve of 7..19).  Host-only
+ * arithmetic; this is the algorithmic work used as a roofline numerator.
+ */
+int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clears);
+
+/* The context's CUDA stream (a cudaStream_t) -- for event timing by callers. */
+void *sieve_stream(sieve_ctx *ctx);
+
+/* Static name of an error code. */
+const char *sieve_strerror(int code);
+
+/* The context's last error message ("" if none); valid until the next call. */
+const char *sieve_last_error(sieve_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSIEVE_H */

@@ -1,1 +1,325 @@
-"""gbsieve: segmented sieve of Eratosthenes on GB300 (sm_103a)."""
+"""gbsieve: the segmented sieve of Eratosthenes on one GB300 (sm_103a).
+
+A thin ctypes binding over ``libgbsieve.so`` (the C ABI in
+``include/gbsieve.h``).  Functions keep the C names and only marshal
+arguments: every step of the sieve runs in the library's CUDA kernels.
+PyTorch supplies device memory (output tensors) and streams.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgbsieve.so")
+
+SIEVE_OK = 0
+SIEVE_EINVAL = -1
+SIEVE_ERANGE = -2
+SIEVE_ETRUNC = -3
+SIEVE_ENOMEM = -4
+SIEVE_ECUDA = -5
+SIEVE_ETIMEOUT = -6
+SIEVE_EBUSY = -7
+SIEVE_ENOENT = -8
+SIEVE_EDEVICE = -9
+
+SIEVE_PARAM_SEGMENT_BYTES = 1
+SIEVE_PARAM_THREADS = 2
+SIEVE_PARAM_SMALL_LIMIT = 3
+SIEVE_PARAM_CTAS_PER_SM = 4
+
+_u64 = ctypes.c_uint64
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_int = ctypes.c_int
+_sz = ctypes.c_size_t
+_pu64 = ctypes.POINTER(ctypes.c_uint64)
+_pu32 = ctypes.POINTER(ctypes.c_uint32)
+
+
+class sieve_info(ctypes.Structure):
+    _fields_ = [("hi_max", _u64), ("prime_limit", _u64), ("n_base_primes", _u64),
+                ("device", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("device_bytes", _u64)]
+
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "sieve_create": (_int, [ctypes.POINTER(_vp), _u64, _int, _vp]),
+    "sieve_destroy": (None, [_vp]),
+    "sieve_count": (_int, [_vp, _u64, _u64, _pu64]),
+    "sieve_count_dev": (_int, [_vp, _u64, _u64, _vp]),
+    "sieve_bitmap": (_int, [_vp, _u64, _u64, _vp, _sz, _pu64]),
+    "sieve_bitmap_words": (_u64, [_u64, _u64]),
+    "sieve_list": (_int, [_vp, _u64, _u64, _vp, _sz, _pu64]),
+    "sieve_list64": (_int, [_vp, _u64, _u64, _vp, _sz, _pu64]),
+    "sieve_compact": (_int, [_vp, _vp, _u64, _u64, _vp, _sz, _pu64]),
+    "sieve_batch_count": (_int, [_vp, _pu64, _pu64, _sz, _pu64, ctypes.POINTER(_vp)]),
+    "sieve_set_param": (_int, [_vp, _int, _i64]),
+    "sieve_get_param": (_int, [_vp, _int, ctypes.POINTER(_i64)]),
+    "sieve_get_info": (_int, [_vp, ctypes.POINTER(sieve_info)]),
+    "sieve_base_primes": (_int, [_vp, _pu32, _sz, _pu64]),
+    "sieve_crossing_work": (_int, [_vp, _u64, _u64, _pu64]),
+    "sieve_stream": (_vp, [_vp]),
+    "sieve_strerror": (ctypes.c_char_p, [_int]),
+    "sieve_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libgbsieve.so (building it first if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> Sequence[str]:
+    return tuple(_SIGS)
+
+
+class SieveError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+def sieve_strerror(code: int) -> str:
+    return load_library().sieve_strerror(code).decode()
+
+
+def sieve_last_error(ctx: int) -> str:
+    return load_library().sieve_last_error(ctx).decode()
+
+
+def _check(ctx, rc: int, allow=()):
+    if rc != SIEVE_OK and rc not in allow:
+        lib = load_library()
+        detail = lib.sieve_last_error(ctx).decode() if ctx else ""
+        raise SieveError(rc, f"{lib.sieve_strerror(rc).decode()}: {detail}")
+    return rc
+
+
+def _ptr(t) -> int:
+    """Device pointer of a CUDA tensor (or an int address / None)."""
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def sieve_create(hi_max: int, device: int = 0, stream: Optional[int] = None) -> int:
+    lib = load_library()
+    h = _vp()
+    rc = lib.sieve_create(ctypes.byref(h), hi_max, device, stream or None)
+    if rc != SIEVE_OK:
+        raise SieveError(rc, f"sieve_create failed: {lib.sieve_strerror(rc).decode()}")
+    return h.value
+
+
+def sieve_destroy(ctx: int) -> None:
+    load_library().sieve_destroy(ctx)
+
+
+def sieve_count(ctx: int, lo: int, hi: int) -> int:
+    c = _u64()
+    _check(ctx, load_library().sieve_count(ctx, lo, hi, ctypes.byref(c)))
+    return c.value
+
+
+def sieve_count_dev(ctx: int, lo: int, hi: int, count_dev) -> None:
+    _check(ctx, load_library().sieve_count_dev(ctx, lo, hi, _ptr(count_dev)))
+
+
+def sieve_bitmap_words(lo: int, hi: int) -> int:
+    return int(load_library().sieve_bitmap_words(lo, hi))
+
+
+def sieve_bitmap(ctx: int, lo: int, hi: int, out, out_words: Optional[int] = None) -> int:
+    """Odd-only bitmap into `out` (a CUDA int32/uint32 tensor or a device address); returns the count."""
+    if out_words is None:
+        out_words = out.numel() * out.element_size() // 4 if out is not None and not isinstance(out, int) else 0
+    c = _u64()
+    _check(ctx, load_library().sieve_bitmap(ctx, lo, hi, _ptr(out), out_words, ctypes.byref(c)))
+    return c.value
+
+
+def _list(fn, ctx, lo, hi, out, cap, elem):
+    if cap is None:
+        cap = out.numel() * out.element_size() // elem if out is not None and not isinstance(out, int) else 0
+    n = _u64()
+    rc = fn(ctx, lo, hi, _ptr(out), cap, ctypes.byref(n))
+    _check(ctx, rc, allow=(SIEVE_ETRUNC,))
+    return n.value, rc
+
+
+def sieve_list(ctx: int, lo: int, hi: int, out, cap: Optional[int] = None):
+    """uint32 prime list into `out`; returns (n, rc) with rc SIEVE_OK or SIEVE_ETRUNC."""
+    return _list(load_library().sieve_list, ctx, lo, hi, out, cap, 4)
+
+
+def sieve_list64(ctx: int, lo: int, hi: int, out, cap: Optional[int] = None):
+    return _list(load_library().sieve_list64, ctx, lo, hi, out, cap, 8)
+
+
+def sieve_compact(ctx: int, bitmap, lo: int, hi: int, out, cap: Optional[int] = None):
+    if cap is None:
+        cap = out.numel() * out.element_size() // 4 if out is not None and not isinstance(out, int) else 0
+    n = _u64()
+    rc = load_library().sieve_compact(ctx, _ptr(bitmap), lo, hi, _ptr(out), cap, ctypes.byref(n))
+    _check(ctx, rc, allow=(SIEVE_ETRUNC,))
+    return n.value, rc
+
+
+def sieve_batch_count(ctx: int, lo: Sequence[int], hi: Sequence[int], bitmaps=None):
+    """Counts of m ranges in one launch; `bitmaps` optionally a list of CUDA tensors (or None)."""
+    m = len(lo)
+    if len(hi) != m:
+        raise ValueError("lo and hi differ in length")
+    LoArr = _u64 * max(m, 1)
+    lo_a, hi_a, cnt = LoArr(*lo), LoArr(*hi), LoArr()
+    bm = None
+    if bitmaps is not None:
+        bm = (_vp * max(m, 1))(*[(_ptr(b) or None) for b in bitmaps])
+    _check(ctx, load_library().sieve_batch_count(ctx, lo_a, hi_a, m, cnt, bm))
+    return [int(cnt[i]) for i in range(m)]
+
+
+def sieve_set_param(ctx: int, param: int, value: int) -> None:
+    _check(ctx, load_library().sieve_set_param(ctx, param, value))
+
+
+def sieve_get_param(ctx: int, param: int) -> int:
+    v = _i64()
+    _check(ctx, load_library().sieve_get_param(ctx, param, ctypes.byref(v)))
+    return v.value
+
+
+def sieve_get_info(ctx: int) -> sieve_info:
+    info = sieve_info()
+    _check(ctx, load_library().sieve_get_info(ctx, ctypes.byref(info)))
+    return info
+
+
+def sieve_base_primes(ctx: int):
+    import numpy as np
+    n = _u64()
+    lib = load_library()
+    _check(ctx, lib.sieve_base_primes(ctx, None, 0, ctypes.byref(n)))
+    out = np.zeros(max(n.value, 1), dtype=np.uint32)
+    _check(ctx, lib.sieve_base_primes(ctx, out.ctypes.data_as(_pu32), n.value, ctypes.byref(n)))
+    return out[:n.value]
+
+
+def sieve_crossing_work(ctx: int, lo: int, hi: int) -> int:
+    c = _u64()
+    _check(ctx, load_library().sieve_crossing_work(ctx, lo, hi, ctypes.byref(c)))
+    return c.value
+
+
+def sieve_stream(ctx: int) -> int:
+    return load_library().sieve_stream(ctx) or 0
+
+
+# cudaStreamLegacy: the device's legacy default stream, shared with torch.
+CUDA_STREAM_LEGACY = 1
+
+
+def torch_stream_handle() -> int:
+    """torch's current stream as a cudaStream_t value (legacy default -> 1)."""
+    import torch
+    h = torch.cuda.current_stream().cuda_stream
+    return h if h else CUDA_STREAM_LEGACY
+
+
+class Sieve:
+    """Owns a sieve context; methods mirror the C calls without the ctx argument.
+
+    By default the context runs on torch's current stream, so tensors torch
+    fills or reads are ordered with the sieve's kernels."""
+
+    def __init__(self, hi_max: int, device: int = 0, stream: Optional[int] = None):
+        if stream is None:
+            import torch
+            with torch.cuda.device(device):
+                stream = torch_stream_handle()
+        self.ctx = sieve_create(hi_max, device, stream)
+
+    def close(self):
+        if self.ctx:
+            sieve_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def count(self, lo, hi):
+        return sieve_count(self.ctx, lo, hi)
+
+    def count_dev(self, lo, hi, out):
+        return sieve_count_dev(self.ctx, lo, hi, out)
+
+    def bitmap(self, lo, hi, out=None):
+        import torch
+        if out is None:
+            out = torch.zeros(max(sieve_bitmap_words(lo, hi), 1), dtype=torch.int32, device="cuda")
+        c = sieve_bitmap(self.ctx, lo, hi, out)
+        return out[:sieve_bitmap_words(lo, hi)], c
+
+    def primes(self, lo, hi, dtype64: bool = False):
+        import torch
+        fn = sieve_list64 if dtype64 else sieve_list
+        n, _ = fn(self.ctx, lo, hi, None, 0)
+        out = torch.empty(max(n, 1), dtype=torch.int64 if dtype64 else torch.int32, device="cuda")
+        n2, rc = fn(self.ctx, lo, hi, out)
+        assert rc == SIEVE_OK and n2 == n
+        return out[:n]
+
+    def batch_count(self, lo, hi, bitmaps=None):
+        return sieve_batch_count(self.ctx, lo, hi, bitmaps)
+
+    def set_param(self, param, value):
+        sieve_set_param(self.ctx, param, value)
+
+    def get_param(self, param):
+        return sieve_get_param(self.ctx, param)
+
+    def info(self):
+        return sieve_get_info(self.ctx)
+
+    def base_primes(self):
+        return sieve_base_primes(self.ctx)
+
+    def crossing_work(self, lo, hi):
+        return sieve_crossing_work(self.ctx, lo, hi)
+
+    def stream(self):
+        return sieve_stream(self.ctx)

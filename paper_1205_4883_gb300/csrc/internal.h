@@ -1,0 +1,82 @@
+// internal.h -- types shared by the kernels and the host side of gbsieve.
+//
+// Layout of the mod-30 wheel used by every sieving kernel: wheel byte b holds
+// the eight integers 30 b + r, r in {1, 7, 11, 13, 17, 19, 23, 29} (the
+// residues coprime to 30), bit k <-> residue k in that order.  Multiples of 2,
+// 3 and 5 have no bit.  A segment is a run of consecutive wheel bytes held in
+// shared memory.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbs {
+
+// Pre-sieve period: 7 * 11 * 13 * 17 * 19 wheel bytes.
+constexpr uint32_t kTilePeriod = 323323u;
+// Largest shared-memory segment a launch may use, bytes (227 KB opt-in limit
+// per CTA minus the kernel's static shared memory).
+constexpr uint32_t kMaxSegmentBytes = 229376u;
+// Number of byte-shifted copies of the pattern (one per 16-byte phase).
+constexpr uint32_t kTileCopies = 16u;
+// Index of the first base prime >= 23 in the base-prime array (2, 3, 5, 7,
+// 11, 13, 17, 19 come first).
+constexpr uint32_t kFirstCrossingPrime = 8u;
+
+// One range of a launch.  Segment s of the range covers wheel bytes
+// [Bbase + s S, Bbase + (s + 1) S); Bbase is chosen so that 30 Bbase + 1 is
+// congruent to o0 = lo | 1 modulo 64 and 30 Bbase <= lo (Bbase may be
+// negative, >= -32, when lo < 960): every group of 32 wheel bytes then maps
+// to exactly 15 whole words of the odd-only output bitmap.
+struct RangeDesc {
+    int64_t Bbase;          // wheel byte of segment 0
+    uint64_t lo, hi;        // the half-open range
+    uint64_t item_first;    // launch-wide index of this range's segment 0
+    uint64_t nseg;          // segments in this range
+    uint32_t *bitmap;       // odd-only output (bitmap mode); null: count only
+    uint64_t bitmap_words;  // words of the odd-only bitmap of [lo, hi)
+    uint64_t corr;          // primes the wheel cannot hold (2, 3, 5) in range
+    uint32_t n_use;         // base primes with p * p < hi (prefix length)
+    uint32_t pad;
+};
+static_assert(sizeof(RangeDesc) == 72, "RangeDesc layout");
+
+enum SieveMode : int { kModeCount = 0, kModeBitmap = 1 };
+
+struct SieveLaunch {
+    const RangeDesc *ranges;
+    uint32_t n_ranges;
+    uint64_t n_items;                    // total segments over all ranges
+    unsigned long long *item_counter;    // zeroed before the launch
+    unsigned long long *counts;          // one per range, zeroed before the launch
+    const uint32_t *primes;              // base primes, ascending, 2 first
+    const uint64_t *magic;               // floor((2^64 - 1) / p) per prime
+    uint32_t small_end;                  // primes [8, small_end) crossed warp-cooperatively
+    const uint8_t *tile;                 // kTileCopies shifted copies of the pattern
+    uint64_t tile_stride;                // bytes between copies
+    uint32_t seg_bytes;                  // S, multiple of 32, <= kMaxSegmentBytes
+    int threads;                         // 256, 512 or 1024
+    int grid;                            // persistent CTAs
+};
+
+// Kernel launchers (sieve_kernels.cu).  All enqueue on `stream` and return the
+// CUDA launch status.
+cudaError_t launch_build_tile(uint8_t *tile, uint64_t stride, uint32_t len, cudaStream_t stream);
+cudaError_t launch_tiny_primes(uint32_t *out, uint32_t *n_out, cudaStream_t stream);
+cudaError_t launch_magic(const uint32_t *primes, uint64_t *magic, uint64_t n, cudaStream_t stream);
+cudaError_t launch_sieve(int mode, const SieveLaunch &L, cudaStream_t stream);
+cudaError_t set_sieve_smem_limits();
+
+// Compaction of an odd-only bitmap into a prime list.
+constexpr uint32_t kCompactTileWords = 2048;  // 256 threads x 8 words
+cudaError_t launch_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *tile_counts,
+                             uint64_t ntiles, int grid, cudaStream_t stream);
+cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint64_t ntiles,
+                             unsigned long long *total, cudaStream_t stream);
+cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets,
+                        uint64_t ntiles, uint64_t o0, uint32_t base_index, void *out,
+                        int out64, int grid, cudaStream_t stream);
+cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream);
+
+}  // namespace gbs

@@ -1,0 +1,655 @@
+// sieve_api.cu -- host side of gbsieve: the context (resident base primes,
+// pattern tile, scratch), range planning and the C ABI of include/gbsieve.h.
+//
+// Base primes (Section 1's sqrt bound) are made on the device in three
+// rounds, each using the sieve itself: primes < 256 by trial division, then
+// primes <= min(limit, 65535) by sieving with those, then primes <= limit
+// (limit = floor(sqrt(hi_max - 1)) <= 2^31) by sieving with the primes below
+// 65536.  Every round's output is a list made by the compaction kernels.
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gbsieve.h"
+#include "internal.h"
+
+using namespace gbs;
+
+struct sieve_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t hi_max = 0;
+    uint64_t prime_limit = 0;
+
+    // resident state
+    uint32_t *d_primes = nullptr;
+    uint64_t *d_magic = nullptr;
+    uint64_t n_primes = 0;
+    std::vector<uint32_t> h_primes;
+    uint8_t *d_tile = nullptr;
+    uint64_t tile_stride = 0;
+
+    // per-launch buffers: [0] item counter, [1..] per-range counts
+    unsigned long long *d_acc = nullptr;
+    size_t acc_cap = 0;  // ranges
+    RangeDesc *d_ranges = nullptr;
+    RangeDesc *h_ranges = nullptr;  // pinned
+    unsigned long long *h_acc = nullptr;  // pinned
+    size_t ranges_cap = 0;
+
+    // compaction scratch
+    uint32_t *d_bitmap = nullptr;
+    size_t bitmap_cap = 0;  // words
+    uint32_t *d_tile_counts = nullptr;
+    uint64_t *d_tile_offsets = nullptr;
+    size_t tiles_cap = 0;
+
+    // launch parameters
+    uint32_t seg_bytes = kMaxSegmentBytes;
+    int threads = 1024;
+    uint32_t small_limit = 7168;
+    int ctas_per_sm = 1;
+
+    uint64_t device_bytes = 0;
+    std::string last_error;
+};
+
+namespace {
+
+const char *kNames[] = {"ok", "invalid argument", "range exceeds limit", "output truncated",
+                        "out of memory", "CUDA error", "timed out", "busy", "unknown ticket",
+                        "device-side limit hit"};
+
+int fail(sieve_ctx *c, int code, const std::string &msg) {
+    if (c) c->last_error = msg;
+    return code;
+}
+
+int cuda_fail(sieve_ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(c, SIEVE_ENOMEM, m);
+    return fail(c, SIEVE_ECUDA, m);
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+    } while (0)
+
+uint64_t isqrt64(uint64_t n) {
+    uint64_t r = 0, bit = 1ull << 62;
+    while (bit > n) bit >>= 2;
+    while (bit) {
+        if (n >= r + bit) {
+            n -= r + bit;
+            r = (r >> 1) + bit;
+        } else {
+            r >>= 1;
+        }
+        bit >>= 2;
+    }
+    return r;
+}
+
+uint64_t bitmap_words_of(uint64_t lo, uint64_t hi) {
+    uint64_t o0 = lo | 1;
+    if (o0 >= hi) return 0;
+    uint64_t nbits = (hi - o0 + 1) / 2;
+    return (nbits + 31) / 32;
+}
+
+// Number of base primes p with p * p < hi, i.e. p <= floor(sqrt(hi - 1)).
+uint32_t primes_needed(const std::vector<uint32_t> &primes, uint64_t hi) {
+    if (hi < 2) return 0;
+    uint64_t lim = isqrt64(hi - 1);
+    return (uint32_t)(std::upper_bound(primes.begin(), primes.end(), lim,
+                                       [](uint64_t v, uint32_t p) { return v < p; }) -
+                      primes.begin());
+}
+
+template <typename T>
+int dev_alloc(sieve_ctx *ctx, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "cudaMalloc");
+    }
+    *p = static_cast<T *>(q);
+    ctx->device_bytes += std::max<size_t>(count, 1) * sizeof(T);
+    return SIEVE_OK;
+}
+
+template <typename T>
+void dev_free(sieve_ctx *ctx, T *&p, size_t count) {
+    if (p) {
+        cudaFree(p);
+        ctx->device_bytes -= std::max<size_t>(count, 1) * sizeof(T);
+    }
+    p = nullptr;
+}
+
+int ensure_ranges(sieve_ctx *ctx, size_t m) {
+    if (m <= ctx->ranges_cap) return SIEVE_OK;
+    size_t cap = std::max<size_t>(m, 64);
+    dev_free(ctx, ctx->d_ranges, ctx->ranges_cap);
+    dev_free(ctx, ctx->d_acc, ctx->acc_cap + 1);
+    if (ctx->h_ranges) cudaFreeHost(ctx->h_ranges);
+    if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
+    ctx->h_ranges = nullptr;
+    ctx->h_acc = nullptr;
+    ctx->ranges_cap = ctx->acc_cap = 0;
+    int rc = dev_alloc(ctx, &ctx->d_ranges, cap);
+    if (rc) return rc;
+    rc = dev_alloc(ctx, &ctx->d_acc, cap + 1);
+    if (rc) return rc;
+    CK(cudaMallocHost(&ctx->h_ranges, cap * sizeof(RangeDesc)));
+    CK(cudaMallocHost(&ctx->h_acc, (cap + 1) * sizeof(unsigned long long)));
+    ctx->ranges_cap = ctx->acc_cap = cap;
+    return SIEVE_OK;
+}
+
+int ensure_bitmap(sieve_ctx *ctx, size_t words) {
+    if (words <= ctx->bitmap_cap) return SIEVE_OK;
+    dev_free(ctx, ctx->d_bitmap, ctx->bitmap_cap);
+    ctx->bitmap_cap = 0;
+    int rc = dev_alloc(ctx, &ctx->d_bitmap, words);
+    if (rc) return rc;
+    ctx->bitmap_cap = words;
+    return SIEVE_OK;
+}
+
+int ensure_tiles(sieve_ctx *ctx, size_t ntiles) {
+    if (ntiles <= ctx->tiles_cap) return SIEVE_OK;
+    dev_free(ctx, ctx->d_tile_counts, ctx->tiles_cap);
+    dev_free(ctx, ctx->d_tile_offsets, ctx->tiles_cap);
+    ctx->tiles_cap = 0;
+    int rc = dev_alloc(ctx, &ctx->d_tile_counts, ntiles);
+    if (rc) return rc;
+    rc = dev_alloc(ctx, &ctx->d_tile_offsets, ntiles);
+    if (rc) return rc;
+    ctx->tiles_cap = ntiles;
+    return SIEVE_OK;
+}
+
+// Fill one RangeDesc (item_first is set by the caller).  Segments start at a
+// wheel byte Bbase with 30 Bbase <= lo and 30 Bbase + 1 = (lo | 1) (mod 64).
+RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_bytes,
+                     int mode, uint32_t *bitmap) {
+    RangeDesc r;
+    std::memset(&r, 0, sizeof r);
+    r.lo = lo;
+    r.hi = hi;
+    r.bitmap = bitmap;
+    r.bitmap_words = bitmap_words_of(lo, hi);
+    if (lo >= hi) return r;
+    const uint64_t o0 = lo | 1;
+    // t0 = 0 (mod 30) and t0 = o0 - 1 (mod 64): t0 = 30 x with 15 x = (o0 - 1) / 2 (mod 32),
+    // and 15 is its own inverse mod 32.
+    const uint64_t a = ((o0 - 1) & 63) / 2;
+    const int64_t t0_res = 30 * (int64_t)((15 * a) & 31);  // residue of t0 mod 960
+    int64_t diff = ((int64_t)(lo % 960) - t0_res) % 960;
+    if (diff < 0) diff += 960;
+    const int64_t t0 = (int64_t)lo - diff;  // >= -930
+    r.Bbase = t0 / 30;
+    const uint64_t span = 30ull * seg_bytes;
+    r.nseg = (uint64_t)(((int64_t)hi - t0 + (int64_t)span - 1) / (int64_t)span);
+    r.n_use = primes_needed(primes, hi);
+    uint64_t corr = (lo <= 2 && 2 < hi) ? 1 : 0;
+    if (mode == kModeCount) corr += (lo <= 3 && 3 < hi ? 1 : 0) + (lo <= 5 && 5 < hi ? 1 : 0);
+    r.corr = corr;
+    return r;
+}
+
+// Run the sieve over ranges h_ranges[0..m) already planned (item_first set
+// here).  Counts land in ctx->d_acc[1..m]; no synchronisation.
+int run_sieve(sieve_ctx *ctx, int mode, const uint32_t *primes_dev, const uint64_t *magic_dev, uint32_t small_end,
+              size_t m) {
+    uint64_t items = 0;
+    for (size_t i = 0; i < m; ++i) {
+        ctx->h_ranges[i].item_first = items;
+        items += ctx->h_ranges[i].nseg;
+    }
+    CK(cudaMemcpyAsync(ctx->d_ranges, ctx->h_ranges, m * sizeof(RangeDesc), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_acc, 0, (m + 1) * sizeof(unsigned long long), ctx->stream));
+    SieveLaunch L;
+    L.ranges = ctx->d_ranges;
+    L.n_ranges = (uint32_t)m;
+    L.n_items = items;
+    L.item_counter = ctx->d_acc;
+    L.counts = ctx->d_acc + 1;
+    L.primes = primes_dev;
+    L.magic = magic_dev;
+    L.small_end = small_end;
+    L.tile = ctx->d_tile;
+    L.tile_stride = ctx->tile_stride;
+    L.seg_bytes = ctx->seg_bytes;
+    L.threads = ctx->threads;
+    uint64_t grid = (uint64_t)ctx->num_sms * ctx->ctas_per_sm;
+    L.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(grid, items));
+    CK(launch_sieve(mode, L, ctx->stream));
+    return SIEVE_OK;
+}
+
+uint32_t small_end_for(const std::vector<uint32_t> &primes, uint32_t limit) {
+    uint32_t e = (uint32_t)(std::lower_bound(primes.begin(), primes.end(), limit) - primes.begin());
+    return std::max<uint32_t>(e, kFirstCrossingPrime);
+}
+
+// Compact the odd-only bitmap of [lo, hi) at bitmap_dev into out_dev (uint32 or
+// uint64 values).  *n = number of primes (2 included).
+int compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo, uint64_t hi, void *out_dev, size_t cap,
+            uint64_t *n, int out64) {
+    const uint64_t nwords = bitmap_words_of(lo, hi);
+    const uint32_t two = (lo <= 2 && 2 < hi) ? 1 : 0;
+    const uint64_t ntiles = (nwords + kCompactTileWords - 1) / kCompactTileWords;
+    uint64_t total = 0;
+    if (ntiles) {
+        int rc = ensure_tiles(ctx, ntiles);
+        if (rc) return rc;
+        int grid = ctx->num_sms * 8;
+        CK(launch_tile_popc(bitmap_dev, nwords, ctx->d_tile_counts, ntiles, grid, ctx->stream));
+        CK(launch_tile_scan(ctx->d_tile_counts, ctx->d_tile_offsets, ntiles, ctx->d_acc, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        total = ctx->h_acc[0];
+    }
+    *n = total + two;
+    if (*n > cap) return fail(ctx, SIEVE_ETRUNC, "output capacity below the prime count");
+    if (*n == 0) return SIEVE_OK;
+    if (!out_dev) return fail(ctx, SIEVE_EINVAL, "null output");
+    if (two) CK(launch_put_two(out_dev, out64, ctx->stream));
+    if (ntiles) {
+        int grid = ctx->num_sms * 8;
+        CK(launch_emit(bitmap_dev, nwords, ctx->d_tile_offsets, ntiles, lo | 1, two, out_dev, out64, grid,
+                       ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SIEVE_OK;
+}
+
+// Sieve [0, limit + 1) into the scratch bitmap and compact it into a fresh
+// device array of primes, using the base primes (primes_dev, magic_dev,
+// host copy h) that cover sqrt(limit).
+int primes_upto(sieve_ctx *ctx, uint64_t limit, const std::vector<uint32_t> &h, const uint32_t *primes_dev,
+                const uint64_t *magic_dev, uint32_t **out_dev, std::vector<uint32_t> &out_h) {
+    const uint64_t hi = limit + 1;
+    int rc = ensure_ranges(ctx, 1);
+    if (rc) return rc;
+    rc = ensure_bitmap(ctx, bitmap_words_of(0, hi));
+    if (rc) return rc;
+    ctx->h_ranges[0] = plan_range(h, 0, hi, ctx->seg_bytes, kModeBitmap, ctx->d_bitmap);
+    rc = run_sieve(ctx, kModeBitmap, primes_dev, magic_dev, small_end_for(h, ctx->small_limit), 1);
+    if (rc) return rc;
+    uint64_t n = 0;
+    rc = compact(ctx, ctx->d_bitmap, 0, hi, nullptr, 0, &n, 0);
+    if (rc != SIEVE_ETRUNC && rc != SIEVE_OK) return rc;
+    uint32_t *d = nullptr;
+    rc = dev_alloc(ctx, &d, n);
+    if (rc) return rc;
+    uint64_t n2 = 0;
+    rc = compact(ctx, ctx->d_bitmap, 0, hi, d, n, &n2, 0);
+    if (rc) {
+        dev_free(ctx, d, n);
+        return rc;
+    }
+    out_h.resize(n);
+    CK(cudaMemcpy(out_h.data(), d, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    *out_dev = d;
+    return SIEVE_OK;
+}
+
+int make_base_primes(sieve_ctx *ctx) {
+    // round 1: primes < 256 by trial division
+    uint32_t *d_tiny = nullptr, *d_ntiny = nullptr;
+    int rc = dev_alloc(ctx, &d_tiny, 64);
+    if (rc) return rc;
+    rc = dev_alloc(ctx, &d_ntiny, 1);
+    if (rc) return rc;
+    CK(launch_tiny_primes(d_tiny, d_ntiny, ctx->stream));
+    uint32_t ntiny = 0;
+    CK(cudaMemcpyAsync(&ntiny, d_ntiny, sizeof ntiny, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<uint32_t> h(ntiny);
+    CK(cudaMemcpy(h.data(), d_tiny, ntiny * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    dev_free(ctx, d_ntiny, 1);
+    uint32_t *d_cur = d_tiny;
+    size_t cur_n = 64;
+    uint64_t *d_mag = nullptr;
+    rc = dev_alloc(ctx, &d_mag, cur_n);
+    if (rc) return rc;
+    CK(launch_magic(d_cur, d_mag, h.size(), ctx->stream));
+
+    // rounds 2 and 3
+    const uint64_t stages[2] = {std::min<uint64_t>(ctx->prime_limit, 65535), ctx->prime_limit};
+    for (int st = 0; st < 2; ++st) {
+        const uint64_t lim = stages[st];
+        if (!h.empty() && h.back() >= lim) break;
+        if (st == 1 && lim <= 65535) break;
+        uint32_t *d_next = nullptr;
+        std::vector<uint32_t> h_next;
+        rc = primes_upto(ctx, lim, h, d_cur, d_mag, &d_next, h_next);
+        if (rc) return rc;
+        dev_free(ctx, d_cur, cur_n);
+        dev_free(ctx, d_mag, cur_n);
+        d_cur = d_next;
+        cur_n = h_next.size();
+        h.swap(h_next);
+        rc = dev_alloc(ctx, &d_mag, cur_n);
+        if (rc) return rc;
+        CK(launch_magic(d_cur, d_mag, h.size(), ctx->stream));
+    }
+    // keep primes <= prime_limit
+    size_t keep = std::upper_bound(h.begin(), h.end(), (uint32_t)std::min<uint64_t>(ctx->prime_limit, 0xffffffffu)) -
+                  h.begin();
+    h.resize(keep);
+    ctx->d_primes = d_cur;
+    ctx->d_magic = d_mag;
+    ctx->n_primes = h.size();
+    ctx->h_primes.swap(h);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SIEVE_OK;
+}
+
+int check_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi) {
+    if (!ctx) return SIEVE_EINVAL;
+    if (lo > hi) return fail(ctx, SIEVE_EINVAL, "lo > hi");
+    if (hi > ctx->hi_max) return fail(ctx, SIEVE_ERANGE, "hi exceeds the context's hi_max");
+    return SIEVE_OK;
+}
+
+int set_device(sieve_ctx *ctx) {
+    CK(cudaSetDevice(ctx->device));
+    return SIEVE_OK;
+}
+
+int sieve_bitmap_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, uint64_t *count) {
+    int rc = ensure_ranges(ctx, 1);
+    if (rc) return rc;
+    ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeBitmap, out_dev);
+    rc = run_sieve(ctx, kModeBitmap, ctx->d_primes, ctx->d_magic, small_end_for(ctx->h_primes, ctx->small_limit), 1);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (count) *count = ctx->h_acc[0];
+    return SIEVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sieve_strerror(int code) {
+    int i = -code;
+    if (i < 0 || i >= (int)(sizeof kNames / sizeof kNames[0])) return "unknown error";
+    return kNames[i];
+}
+
+const char *sieve_last_error(sieve_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+uint64_t sieve_bitmap_words(uint64_t lo, uint64_t hi) { return lo > hi ? 0 : bitmap_words_of(lo, hi); }
+
+void *sieve_stream(sieve_ctx *ctx) { return ctx ? (void *)ctx->stream : nullptr; }
+
+int sieve_create(sieve_ctx **out, uint64_t hi_max, int device, void *cuda_stream) {
+    if (!out) return SIEVE_EINVAL;
+    *out = nullptr;
+    if (hi_max < 2 || hi_max > (1ull << 62)) return SIEVE_ERANGE;
+    sieve_ctx *ctx = new (std::nothrow) sieve_ctx;
+    if (!ctx) return SIEVE_ENOMEM;
+    ctx->device = device;
+    ctx->hi_max = hi_max;
+    ctx->prime_limit = isqrt64(hi_max - 1);
+    int rc = SIEVE_OK;
+    auto bail = [&](int code) {
+        sieve_destroy(ctx);
+        return code;
+    };
+    {
+        cudaError_t e = cudaSetDevice(device);
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaSetDevice"));
+        e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaDeviceGetAttribute"));
+        if (cuda_stream) {
+            ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaStreamCreate"));
+            ctx->own_stream = true;
+        }
+        e = set_sieve_smem_limits();
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaFuncSetAttribute"));
+    }
+    // pattern tile: 16 copies, each long enough for any phase plus a full segment
+    const uint64_t len = ((uint64_t)kTilePeriod + kMaxSegmentBytes + 32 + 15) & ~15ull;
+    ctx->tile_stride = len;
+    rc = dev_alloc(ctx, &ctx->d_tile, len * kTileCopies);
+    if (rc) return bail(rc);
+    {
+        cudaError_t e = launch_build_tile(ctx->d_tile, ctx->tile_stride, (uint32_t)len, ctx->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "build tile"));
+    }
+    rc = make_base_primes(ctx);
+    if (rc) return bail(rc);
+    *out = ctx;
+    return SIEVE_OK;
+}
+
+void sieve_destroy(sieve_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_primes);
+    cudaFree(ctx->d_magic);
+    cudaFree(ctx->d_tile);
+    cudaFree(ctx->d_acc);
+    cudaFree(ctx->d_ranges);
+    cudaFree(ctx->d_bitmap);
+    cudaFree(ctx->d_tile_counts);
+    cudaFree(ctx->d_tile_offsets);
+    if (ctx->h_ranges) cudaFreeHost(ctx->h_ranges);
+    if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count) {
+    if (!count) return fail(ctx, SIEVE_EINVAL, "null count");
+    int rc = check_range(ctx, lo, hi);
+    if (rc) return rc;
+    if ((rc = set_device(ctx))) return rc;
+    if (lo == hi) {
+        *count = 0;
+        return SIEVE_OK;
+    }
+    rc = ensure_ranges(ctx, 1);
+    if (rc) return rc;
+    ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeCount, nullptr);
+    rc = run_sieve(ctx, kModeCount, ctx->d_primes, ctx->d_magic, small_end_for(ctx->h_primes, ctx->small_limit), 1);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *count = ctx->h_acc[0];
+    return SIEVE_OK;
+}
+
+int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_dev) {
+    if (!count_dev) return fail(ctx, SIEVE_EINVAL, "null count");
+    int rc = check_range(ctx, lo, hi);
+    if (rc) return rc;
+    if ((rc = set_device(ctx))) return rc;
+    rc = ensure_ranges(ctx, 1);
+    if (rc) return rc;
+    ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeCount, nullptr);
+    rc = run_sieve(ctx, kModeCount, ctx->d_primes, ctx->d_magic, small_end_for(ctx->h_primes, ctx->small_limit), 1);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(count_dev, ctx->d_acc + 1, sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream));
+    return SIEVE_OK;
+}
+
+int sieve_bitmap(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, size_t out_words, uint64_t *count) {
+    int rc = check_range(ctx, lo, hi);
+    if (rc) return rc;
+    if ((rc = set_device(ctx))) return rc;
+    const uint64_t need = bitmap_words_of(lo, hi);
+    if (out_words < need) return fail(ctx, SIEVE_ETRUNC, "bitmap capacity too small");
+    if (need && !out_dev) return fail(ctx, SIEVE_EINVAL, "null bitmap");
+    if (lo == hi) {
+        if (count) *count = 0;
+        return SIEVE_OK;
+    }
+    return sieve_bitmap_into(ctx, lo, hi, out_dev, count);
+}
+
+static int list_impl(sieve_ctx *ctx, uint64_t lo, uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64) {
+    if (!n) return fail(ctx, SIEVE_EINVAL, "null n");
+    int rc = check_range(ctx, lo, hi);
+    if (rc) return rc;
+    if (!out64 && hi > (1ull << 32)) return fail(ctx, SIEVE_ERANGE, "uint32 list needs hi <= 2^32");
+    if ((rc = set_device(ctx))) return rc;
+    if (lo == hi) {
+        *n = 0;
+        return SIEVE_OK;
+    }
+    rc = ensure_bitmap(ctx, bitmap_words_of(lo, hi));
+    if (rc) return rc;
+    rc = sieve_bitmap_into(ctx, lo, hi, ctx->d_bitmap, nullptr);
+    if (rc) return rc;
+    return compact(ctx, ctx->d_bitmap, lo, hi, out_dev, cap, n, out64);
+}
+
+int sieve_list(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, size_t cap, uint64_t *n) {
+    return list_impl(ctx, lo, hi, out_dev, cap, n, 0);
+}
+
+int sieve_list64(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out_dev, size_t cap, uint64_t *n) {
+    return list_impl(ctx, lo, hi, out_dev, cap, n, 1);
+}
+
+int sieve_compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo, uint64_t hi, uint32_t *out_dev,
+                  size_t cap, uint64_t *n) {
+    if (!n) return fail(ctx, SIEVE_EINVAL, "null n");
+    int rc = check_range(ctx, lo, hi);
+    if (rc) return rc;
+    if (hi > (1ull << 32)) return fail(ctx, SIEVE_ERANGE, "uint32 list needs hi <= 2^32");
+    if (bitmap_words_of(lo, hi) && !bitmap_dev) return fail(ctx, SIEVE_EINVAL, "null bitmap");
+    if ((rc = set_device(ctx))) return rc;
+    rc = ensure_ranges(ctx, 1);
+    if (rc) return rc;
+    return compact(ctx, bitmap_dev, lo, hi, out_dev, cap, n, 0);
+}
+
+int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t m, uint64_t *counts,
+                      uint32_t *const *bitmaps_dev) {
+    if (!ctx) return SIEVE_EINVAL;
+    if (m == 0) return SIEVE_OK;
+    if (!lo || !hi || !counts) return fail(ctx, SIEVE_EINVAL, "null array");
+    for (size_t i = 0; i < m; ++i) {
+        int rc = check_range(ctx, lo[i], hi[i]);
+        if (rc) return rc;
+    }
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    rc = ensure_ranges(ctx, m);
+    if (rc) return rc;
+    const int mode = bitmaps_dev ? kModeBitmap : kModeCount;
+    for (size_t i = 0; i < m; ++i) {
+        uint32_t *bm = bitmaps_dev ? bitmaps_dev[i] : nullptr;
+        ctx->h_ranges[i] = plan_range(ctx->h_primes, lo[i], hi[i], ctx->seg_bytes, mode, bm);
+    }
+    rc = run_sieve(ctx, mode, ctx->d_primes, ctx->d_magic, small_end_for(ctx->h_primes, ctx->small_limit), m);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, m * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < m; ++i) counts[i] = ctx->h_acc[i];
+    return SIEVE_OK;
+}
+
+int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
+    if (!ctx) return SIEVE_EINVAL;
+    switch (param) {
+        case SIEVE_PARAM_SEGMENT_BYTES:
+            if (v < 1024 || v > (int64_t)kMaxSegmentBytes || v % 32) return fail(ctx, SIEVE_EINVAL, "segment bytes");
+            ctx->seg_bytes = (uint32_t)v;
+            return SIEVE_OK;
+        case SIEVE_PARAM_THREADS:
+            if (v != 256 && v != 512 && v != 1024) return fail(ctx, SIEVE_EINVAL, "threads");
+            ctx->threads = (int)v;
+            return SIEVE_OK;
+        case SIEVE_PARAM_SMALL_LIMIT:
+            if (v < 23 || v > 65536) return fail(ctx, SIEVE_EINVAL, "small limit");
+            ctx->small_limit = (uint32_t)v;
+            return SIEVE_OK;
+        case SIEVE_PARAM_CTAS_PER_SM:
+            if (v < 1 || v > 8) return fail(ctx, SIEVE_EINVAL, "ctas per sm");
+            ctx->ctas_per_sm = (int)v;
+            return SIEVE_OK;
+        default:
+            return fail(ctx, SIEVE_EINVAL, "unknown parameter");
+    }
+}
+
+int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
+    if (!ctx || !v) return SIEVE_EINVAL;
+    switch (param) {
+        case SIEVE_PARAM_SEGMENT_BYTES: *v = ctx->seg_bytes; return SIEVE_OK;
+        case SIEVE_PARAM_THREADS: *v = ctx->threads; return SIEVE_OK;
+        case SIEVE_PARAM_SMALL_LIMIT: *v = ctx->small_limit; return SIEVE_OK;
+        case SIEVE_PARAM_CTAS_PER_SM: *v = ctx->ctas_per_sm; return SIEVE_OK;
+        default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");
+    }
+}
+
+int sieve_get_info(sieve_ctx *ctx, sieve_info *info) {
+    if (!ctx || !info) return SIEVE_EINVAL;
+    info->hi_max = ctx->hi_max;
+    info->prime_limit = ctx->prime_limit;
+    info->n_base_primes = ctx->n_primes;
+    info->device = ctx->device;
+    info->num_sms = ctx->num_sms;
+    info->device_bytes = ctx->device_bytes;
+    return SIEVE_OK;
+}
+
+int sieve_base_primes(sieve_ctx *ctx, uint32_t *out, size_t cap, uint64_t *n) {
+    if (!ctx || !n) return SIEVE_EINVAL;
+    *n = ctx->h_primes.size();
+    if (out) std::memcpy(out, ctx->h_primes.data(), std::min<size_t>(cap, ctx->h_primes.size()) * sizeof(uint32_t));
+    return SIEVE_OK;
+}
+
+int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clears) {
+    if (!clears) return fail(ctx, SIEVE_EINVAL, "null clears");
+    int rc = check_range(ctx, lo, hi);
+    if (rc) return rc;
+    // For each base prime p >= 23: #{ m : m >= p, gcd(m, 30) = 1, lo <= p m < hi }.
+    auto coprime30_below = [](uint64_t x) -> uint64_t {  // #{ 1 <= m < x : gcd(m, 30) = 1 }
+        static const uint8_t cum[31] = {0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 4, 4, 4,
+                                        4, 5, 5, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 8};
+        if (x == 0) return 0;
+        return (x / 30) * 8 + cum[x % 30];
+    };
+    uint64_t total = 0;
+    const uint32_t n_use = primes_needed(ctx->h_primes, hi);
+    for (uint32_t i = kFirstCrossingPrime; i < n_use; ++i) {
+        const uint64_t p = ctx->h_primes[i];
+        uint64_t m_lo = std::max<uint64_t>(p, (lo + p - 1) / p);
+        uint64_t m_hi = (hi + p - 1) / p;  // m < m_hi  <=>  p m < hi
+        if (m_hi > m_lo) total += coprime30_below(m_hi) - coprime30_below(m_lo);
+    }
+    *clears = total;
+    return SIEVE_OK;
+}
+
+}  // extern "C"

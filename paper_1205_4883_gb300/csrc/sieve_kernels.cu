@@ -1,0 +1,511 @@
+// sieve_kernels.cu -- the GB300 kernels of the segmented sieve of Eratosthenes.
+//
+// Paper, Section 3.1: the sieve marks as composite the multiples of each
+// prime; Section 1: primes <= sqrt(hi - 1) suffice for [lo, hi); Eq. 3: the
+// integers are processed in blocks ("segments"), the last one short.
+//
+// Data layout: a segment is S consecutive mod-30 wheel bytes (30 S integers)
+// in shared memory; wheel byte b, bit k <-> integer 30 b + r_k with
+// r = {1, 7, 11, 13, 17, 19, 23, 29}.  Per segment a CTA
+//   1. copies the pre-sieved pattern (multiples of 7, 11, 13, 17, 19 already
+//      cleared; period 323323 bytes) from one of 16 byte-shifted copies held
+//      in L2, so every copy is 16-byte aligned;
+//   2. crosses off, for every base prime p >= 23 and every wheel class j, the
+//      arithmetic progression of multiples p m with m = r_j (mod 30), m >= p:
+//      in wheel bytes it is c_j + p q (c_j = floor(p r_j / 30)) with a fixed
+//      bit -- "small" primes (many hits per class) are crossed by a whole warp
+//      striding over one progression, the rest by one thread per prime;
+//   3. counts the surviving bits in [lo, hi) (__popc + warp shuffles) or
+//      expands them into the odd-only bitmap in HBM.
+// CTAs are persistent and take segments from a global counter.
+
+#include "internal.h"
+
+namespace gbs {
+namespace {
+
+__constant__ uint32_t c_res[8] = {1, 7, 11, 13, 17, 19, 23, 29};
+
+struct WheelTables {
+    uint16_t expand[256];  // wheel byte -> 15 odd-only bits (odd integers 30b+1 .. 30b+29)
+    uint8_t adj[64];       // [class of p][j]: floor(r_c * r_j / 30)
+    uint8_t bit[64];       // [class of p][j]: wheel bit of (r_c * r_j) mod 30
+    uint8_t cls[32];       // residue mod 30 -> wheel class (0xff if not coprime)
+};
+
+__device__ __forceinline__ int wheel_index(uint32_t r) {
+    int k = -1;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (c_res[i] == r) k = i;
+    return k;
+}
+
+__device__ void init_tables(WheelTables &t) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        uint32_t e = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (i & (1 << k)) e |= 1u << ((c_res[k] - 1) / 2);
+        t.expand[i] = (uint16_t)e;
+    }
+    if (threadIdx.x < 64) {
+        int c = threadIdx.x >> 3, j = threadIdx.x & 7;
+        uint32_t prod = c_res[c] * c_res[j];
+        t.adj[threadIdx.x] = (uint8_t)(prod / 30);
+        t.bit[threadIdx.x] = (uint8_t)wheel_index(prod % 30);
+    }
+    if (threadIdx.x < 32) {
+        int k = wheel_index(threadIdx.x);
+        t.cls[threadIdx.x] = (uint8_t)(k < 0 ? 0xff : k);
+    }
+}
+
+// x mod p by Barrett reduction with M = floor((2^64 - 1) / p): the quotient
+// estimate umulhi(x, M) is floor(x / p) or one less, so one correction step.
+__device__ __forceinline__ uint32_t mod_barrett(uint64_t x, uint32_t p, uint64_t M) {
+    uint64_t q = __umul64hi(x, M);
+    uint64_t r = x - q * (uint64_t)p;
+    return (uint32_t)(r >= p ? r - p : r);
+}
+
+__device__ __forceinline__ void clear_bit(uint32_t *seg32, uint32_t off, uint32_t bit) {
+    atomicAnd(&seg32[off >> 2], ~(1u << (((off & 3u) << 3) | bit)));
+}
+
+// First byte offset (relative to B0) of progression j of prime p in a segment
+// starting at wheel byte B0; Bc = max(B0, 0), R = Bc mod p.  Returns a value
+// >= L when the progression misses the first L bytes.
+struct ClassStart {
+    uint32_t off;
+    uint32_t bit;
+};
+
+__device__ __forceinline__ ClassStart class_start(const WheelTables &t, uint32_t p, uint32_t pq, uint32_t pc,
+                                                  int j, uint32_t R, int64_t B0, uint64_t Bc, bool early,
+                                                  uint32_t L) {
+    uint32_t cj = pq * c_res[j] + t.adj[pc * 8 + j];
+    int32_t d = (int32_t)(cj - R);
+    if (d < 0) d += (int32_t)p;
+    uint64_t start = Bc + (uint32_t)d;
+    if (early) {
+        // multiples p m with m < p are left alone: m = 30 q + r_j >= p
+        uint32_t rj = c_res[j];
+        uint64_t q0 = p > rj ? (uint64_t)((p - rj + 29) / 30) : 0;
+        uint64_t bmin = (uint64_t)p * q0 + cj;
+        if (bmin > start) start = bmin;
+    }
+    int64_t off = (int64_t)start - B0;
+    ClassStart cs;
+    cs.off = off < (int64_t)L ? (uint32_t)off : L;
+    cs.bit = t.bit[pc * 8 + j];
+    return cs;
+}
+
+// Bits of wheel word w (4 bytes at integers base .. base + 119, base relative
+// to 30 B0) that lie in [lo_rel, hi_rel).
+__device__ uint32_t range_mask(int64_t base, int64_t lo_rel, int64_t hi_rel) {
+    uint32_t m = 0;
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 8; ++k) {
+            int64_t n = base + 30 * i + c_res[k];
+            if (n >= lo_rel && n < hi_rel) m |= 1u << (8 * i + k);
+        }
+    return m;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(1024, 1) k_sieve(SieveLaunch P) {
+    extern __shared__ uint4 smem4[];
+    uint8_t *seg = reinterpret_cast<uint8_t *>(smem4);
+    uint32_t *seg32 = reinterpret_cast<uint32_t *>(smem4);
+    __shared__ WheelTables tab;
+    __shared__ unsigned long long s_item;
+    __shared__ uint32_t s_range;
+    __shared__ uint32_t s_small_next;
+    __shared__ unsigned long long s_red[32];
+
+    init_tables(tab);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t S = P.seg_bytes;
+
+    for (;;) {
+        if (tid == 0) {
+            unsigned long long item = atomicAdd(P.item_counter, 1ull);
+            s_item = item;
+            if (item < P.n_items) {
+                uint32_t a = 0, b = P.n_ranges - 1;  // largest r with item_first <= item
+                while (a < b) {
+                    uint32_t mid = (a + b + 1) >> 1;
+                    if (P.ranges[mid].item_first <= item) a = mid; else b = mid - 1;
+                }
+                s_range = a;
+            }
+            s_small_next = 0;
+        }
+        __syncthreads();
+        const unsigned long long item = s_item;
+        if (item >= P.n_items) break;
+        const RangeDesc &rd = P.ranges[s_range];
+        const uint64_t s = item - rd.item_first;
+        const int64_t B0 = rd.Bbase + (int64_t)(s * S);
+        const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
+        const int64_t base_int = 30 * B0;  // integer of bit 0 of byte 0
+        const int64_t hi_rel = (int64_t)rd.hi - base_int, lo_rel = (int64_t)rd.lo - base_int;
+        uint32_t L;
+        {
+            int64_t need = (hi_rel + 29) / 30;
+            need = (need + 31) & ~(int64_t)31;
+            L = need < (int64_t)S ? (uint32_t)need : S;
+        }
+        const uint32_t n_use = rd.n_use;
+        const uint32_t small_end = P.small_end < n_use ? P.small_end : n_use;
+        const uint32_t n_small8 = (small_end > kFirstCrossingPrime ? small_end - kFirstCrossingPrime : 0) * 8;
+
+        // 1. pre-sieved pattern -> shared memory (16-byte aligned copy)
+        {
+            int64_t ph = B0 % (int64_t)kTilePeriod;
+            if (ph < 0) ph += kTilePeriod;
+            const uint32_t k = (uint32_t)ph & 15u;
+            const uint4 *src = reinterpret_cast<const uint4 *>(P.tile + k * P.tile_stride + ((uint32_t)ph - k));
+            for (uint32_t i = tid; i < L / 16; i += blockDim.x) smem4[i] = __ldg(src + i);
+        }
+        __syncthreads();
+
+        // 2a. one thread per prime for primes [small_end, n_use)
+        for (uint32_t i = P.small_end + tid; i < n_use; i += blockDim.x) {
+            const uint32_t p = __ldg(P.primes + i);
+            const uint64_t M = __ldg(P.magic + i);
+            const uint32_t R = mod_barrett(Bc, p, M);
+            const uint32_t pq = p / 30, pc = tab.cls[p - pq * 30];
+            const bool early = Bc < ((uint64_t)p * p) / 30 + 2ull * p + 2ull;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                ClassStart cs = class_start(tab, p, pq, pc, j, R, B0, Bc, early, L);
+                for (uint32_t o = cs.off; o < L; o += p) clear_bit(seg32, o, cs.bit);
+            }
+        }
+        // 2b. warp-cooperative: one (prime, class) progression per warp, lanes
+        //     striding by 32 p; items in decreasing order of hits, taken dynamically
+        for (;;) {
+            uint32_t k = 0;
+            if (lane == 0) k = atomicAdd(&s_small_next, 1u);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k >= n_small8) break;
+            const uint32_t i = kFirstCrossingPrime + (k >> 3);
+            const int j = (int)(k & 7);
+            const uint32_t p = __ldg(P.primes + i);
+            const uint64_t M = __ldg(P.magic + i);
+            const uint32_t R = mod_barrett(Bc, p, M);
+            const uint32_t pq = p / 30, pc = tab.cls[p - pq * 30];
+            const bool early = Bc < ((uint64_t)p * p) / 30 + 2ull * p + 2ull;
+            ClassStart cs;
+            switch (j) {  // keep j a compile-time index into c_res
+                case 0: cs = class_start(tab, p, pq, pc, 0, R, B0, Bc, early, L); break;
+                case 1: cs = class_start(tab, p, pq, pc, 1, R, B0, Bc, early, L); break;
+                case 2: cs = class_start(tab, p, pq, pc, 2, R, B0, Bc, early, L); break;
+                case 3: cs = class_start(tab, p, pq, pc, 3, R, B0, Bc, early, L); break;
+                case 4: cs = class_start(tab, p, pq, pc, 4, R, B0, Bc, early, L); break;
+                case 5: cs = class_start(tab, p, pq, pc, 5, R, B0, Bc, early, L); break;
+                case 6: cs = class_start(tab, p, pq, pc, 6, R, B0, Bc, early, L); break;
+                default: cs = class_start(tab, p, pq, pc, 7, R, B0, Bc, early, L); break;
+            }
+            const uint32_t step = 32u * p;
+            for (uint32_t o = cs.off + (uint32_t)lane * p; o < L; o += step) clear_bit(seg32, o, cs.bit);
+        }
+        __syncthreads();
+
+        // 3. the byte holding integers 0..29: 1 is not prime, 7..19 are
+        if (tid == 0 && B0 <= 0 && B0 + (int64_t)L > 0) seg[-B0] = 0xFE;
+        __syncthreads();
+
+        unsigned long long cnt = 0;
+        if (MODE == kModeCount) {
+            // 4. popcount of the bits in [lo, hi)
+            for (uint32_t w = tid; w < L / 4; w += blockDim.x) {
+                uint32_t v = seg32[w];
+                const int64_t wb = 120 * (int64_t)w;
+                if (wb < lo_rel || wb + 120 > hi_rel) v &= range_mask(wb, lo_rel, hi_rel);
+                cnt += __popc(v);
+            }
+        } else {
+            // 4'. expand each group of 32 wheel bytes (960 integers) into 15
+            //     words of the odd-only bitmap and store them
+            const uint64_t nwords = rd.bitmap_words;
+            const uint64_t o0 = rd.lo | 1;
+            const uint64_t nbits = o0 < rd.hi ? (rd.hi - o0 + 1) / 2 : 0;
+            uint32_t *out = rd.bitmap;
+            for (uint32_t g = tid; g < L / 32; g += blockDim.x) {
+                const int64_t n0 = base_int + 960 * (int64_t)g + 1;  // first odd integer of the group
+                const int64_t w0 = (n0 - (int64_t)o0) / 64;         // exact: n0 = o0 (mod 64)
+                if (w0 + 15 <= 0 || w0 >= (int64_t)nwords) continue;
+                uint32_t wv[8];
+                const uint4 a = smem4[2 * g], b = smem4[2 * g + 1];
+                wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
+                wv[4] = b.x; wv[5] = b.y; wv[6] = b.z; wv[7] = b.w;
+                uint32_t o[15];
+#pragma unroll
+                for (int q = 0; q < 15; ++q) o[q] = 0;
+#pragma unroll
+                for (int bb = 0; bb < 32; ++bb) {
+                    const uint32_t e = tab.expand[(wv[bb >> 2] >> (8 * (bb & 3))) & 0xffu];
+                    const int pos = 15 * bb, wi = pos >> 5, sh = pos & 31;
+                    o[wi] |= e << sh;
+                    if (sh > 17) o[wi + 1] |= e >> (32 - sh);
+                }
+                // 3 and 5 are prime but have no wheel bit
+                if (n0 <= 5 && n0 + 958 >= 3) {
+#pragma unroll
+                    for (int sp = 3; sp <= 5; sp += 2) {
+                        const int64_t k = (sp - n0) / 2;
+                        if (sp >= n0 && k < 480) {
+#pragma unroll
+                            for (int q = 0; q < 15; ++q)  // compile-time register index
+                                if ((k >> 5) == q) o[q] |= 1u << (k & 31);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 15; ++q) {
+                    const int64_t wq = w0 + q;
+                    if (wq < 0 || wq >= (int64_t)nwords) continue;
+                    uint32_t v = o[q];
+                    if (wq == (int64_t)nwords - 1 && (nbits & 31)) v &= (1u << (nbits & 31)) - 1u;
+                    if (out) out[wq] = v;
+                    cnt += __popc(v);
+                }
+            }
+        }
+        cnt = warp_sum(cnt);
+        if (lane == 0) s_red[tid >> 5] = cnt;
+        __syncthreads();
+        if (tid < 32) {
+            unsigned long long v = tid < (int)(blockDim.x >> 5) ? s_red[tid] : 0ull;
+            v = warp_sum(v);
+            if (tid == 0) {
+                if (s == 0) v += rd.corr;
+                atomicAdd(P.counts + s_range, v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- pattern tile
+
+// Copy k (k = blockIdx.y) holds pattern bytes (i + k) mod 323323 at offset i.
+// Pattern byte b, bit j: 1 iff 30 b + r_j has no prime factor among 7..19.
+__global__ void k_build_tile(uint8_t *tile, uint64_t stride, uint32_t len) {
+    const uint32_t k = blockIdx.y;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+        const uint32_t b = (i + k) % kTilePeriod;
+        uint32_t v = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t n = 30u * b + c_res[j];
+            if (n % 7u && n % 11u && n % 13u && n % 17u && n % 19u) v |= 1u << j;
+        }
+        tile[k * stride + i] = (uint8_t)v;
+    }
+}
+
+// Primes below 256 by trial division, ascending, one block of 256 threads.
+__global__ void k_tiny_primes(uint32_t *out, uint32_t *n_out) {
+    __shared__ uint32_t warp_cnt[8];
+    const uint32_t n = threadIdx.x;
+    bool prime = n >= 2;
+    for (uint32_t d = 2; d * d <= n; ++d)
+        if (n % d == 0) prime = false;
+    const uint32_t ballot = __ballot_sync(0xffffffffu, prime);
+    const int lane = n & 31, warp = n >> 5;
+    if (lane == 0) warp_cnt[warp] = __popc(ballot);
+    __syncthreads();
+    uint32_t base = 0;
+    for (int w = 0; w < warp; ++w) base += warp_cnt[w];
+    if (prime) out[base + __popc(ballot & ((1u << lane) - 1u))] = n;
+    if (n == 255) *n_out = base + __popc(ballot);
+}
+
+__global__ void k_magic(const uint32_t *primes, uint64_t *magic, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        magic[i] = ~0ull / primes[i];
+}
+
+// ---------------------------------------------------------------- compaction
+
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t wbase = 0, all = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (w < warp) wbase += s_warp[w];
+        all += s_warp[w];
+    }
+    *total = all;
+    return wbase + x - v;
+}
+
+__global__ void __launch_bounds__(256) k_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *tile_counts,
+                                                   uint64_t ntiles) {
+    __shared__ uint32_t s_warp[8];
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t w0 = t * kCompactTileWords + threadIdx.x * 8ull;
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (w0 + k < nwords) c += __popc(__ldg(bitmap + w0 + k));
+        uint32_t total;
+        block_exclusive_scan_256(c, s_warp, &total);
+        if (threadIdx.x == 0) tile_counts[t] = total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t *tile_counts, uint64_t *tile_offsets,
+                                                    uint64_t ntiles, unsigned long long *total) {
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_run;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_run = 0;
+    __syncthreads();
+    for (uint64_t base = 0; base < ntiles; base += blockDim.x) {
+        const uint64_t t = base + threadIdx.x;
+        const unsigned long long v = t < ntiles ? tile_counts[t] : 0ull;
+        unsigned long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        unsigned long long wbase = 0, all = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) wbase += s_warp[w];
+            all += s_warp[w];
+        }
+        if (t < ntiles) tile_offsets[t] = s_run + wbase + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) s_run += all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = s_run;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets,
+                                              uint64_t ntiles, uint64_t o0, uint32_t base_index, T *out) {
+    __shared__ uint32_t s_warp[8];
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t w0 = t * kCompactTileWords + threadIdx.x * 8ull;
+        uint32_t w[8];
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            w[k] = (w0 + k < nwords) ? __ldg(bitmap + w0 + k) : 0u;
+            c += __popc(w[k]);
+        }
+        uint32_t total;
+        uint64_t pos = base_index + tile_offsets[t] + block_exclusive_scan_256(c, s_warp, &total);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            uint32_t v = w[k];
+            while (v) {
+                const int b = __ffs(v) - 1;
+                v &= v - 1;
+                out[pos++] = (T)(o0 + 2ull * ((w0 + k) * 32ull + b));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_put_two(T *out) { out[0] = (T)2; }
+
+}  // namespace
+
+cudaError_t set_sieve_smem_limits() {
+    const int bytes = (int)kMaxSegmentBytes;
+    cudaError_t e = cudaFuncSetAttribute(k_sieve<kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sieve<kModeBitmap>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_sieve(int mode, const SieveLaunch &L, cudaStream_t stream) {
+    if (L.n_items == 0) return cudaSuccess;
+    const size_t smem = L.seg_bytes;
+    if (mode == kModeCount)
+        k_sieve<kModeCount><<<L.grid, L.threads, smem, stream>>>(L);
+    else
+        k_sieve<kModeBitmap><<<L.grid, L.threads, smem, stream>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_tile(uint8_t *tile, uint64_t stride, uint32_t len, cudaStream_t stream) {
+    dim3 grid((len + 255) / 256 < 4096 ? (len + 255) / 256 : 4096, kTileCopies);
+    k_build_tile<<<grid, 256, 0, stream>>>(tile, stride, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tiny_primes(uint32_t *out, uint32_t *n_out, cudaStream_t stream) {
+    k_tiny_primes<<<1, 256, 0, stream>>>(out, n_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_magic(const uint32_t *primes, uint64_t *magic, uint64_t n, cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    k_magic<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, stream>>>(primes, magic, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *tile_counts, uint64_t ntiles,
+                             int grid, cudaStream_t stream) {
+    if (ntiles == 0) return cudaSuccess;
+    unsigned g = (unsigned)(ntiles < (uint64_t)grid ? ntiles : (uint64_t)grid);
+    k_tile_popc<<<g, 256, 0, stream>>>(bitmap, nwords, tile_counts, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint64_t ntiles,
+                             unsigned long long *total, cudaStream_t stream) {
+    k_tile_scan<<<1, 1024, 0, stream>>>(tile_counts, tile_offsets, ntiles, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets, uint64_t ntiles,
+                        uint64_t o0, uint32_t base_index, void *out, int out64, int grid, cudaStream_t stream) {
+    if (ntiles == 0) return cudaSuccess;
+    unsigned g = (unsigned)(ntiles < (uint64_t)grid ? ntiles : (uint64_t)grid);
+    if (out64)
+        k_emit<uint64_t><<<g, 256, 0, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
+                                                static_cast<uint64_t *>(out));
+    else
+        k_emit<uint32_t><<<g, 256, 0, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
+                                                static_cast<uint32_t *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream) {
+    if (out64)
+        k_put_two<uint64_t><<<1, 1, 0, stream>>>(static_cast<uint64_t *>(out));
+    else
+        k_put_two<uint32_t><<<1, 1, 0, stream>>>(static_cast<uint32_t *>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace gbs

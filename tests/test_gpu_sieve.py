@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA sieve (through the C ABI) against the CPU oracle,
+element by element, bit-exact.  Marked gpu."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from numtheory import load_golden, mr_is_prime, td_is_prime
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only hosts
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1205_4883_gb300 as gb  # noqa: E402
+from paper_1205_4883_gb300.workloads import batch_intervals, random_ranges  # noqa: E402
+
+PI = {int(x): int(v) for x, v in load_golden("pi_values.txt")}
+HI_MAX = 1 << 47  # covers 10^14 + 10^8 (batched) and 10^12 + 10^9 (served)
+
+
+@pytest.fixture(scope="module")
+def sv():
+    s = gb.Sieve(HI_MAX)
+    yield s
+    s.close()
+
+
+def gpu_bitmap(sv, lo, hi):
+    words, c = sv.bitmap(lo, hi)
+    return words.cpu().numpy().view(np.uint32), c
+
+
+def test_base_primes_match_oracle(sv):
+    info = sv.info()
+    assert info.prime_limit == math.isqrt(HI_MAX - 1)
+    assert np.array_equal(sv.base_primes(), oracle.base_primes(info.prime_limit))
+
+
+def test_pi_1e7_count_bitmap_list(sv):
+    lo, hi = 0, 10**7
+    assert sv.count(lo, hi) == PI[10**7]
+    words, c = gpu_bitmap(sv, lo, hi)
+    assert c == PI[10**7]
+    assert np.array_equal(words, oracle.bitmap(lo, hi))
+    lst = sv.primes(lo, hi).cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(lst, oracle.primes(lo, hi))
+    assert lst[-1] == 9_999_991
+
+
+def test_all_small_ranges_brute_force(sv):
+    # every 0 <= lo <= hi <= 2000, batched, against trial division
+    mask = np.array([td_is_prime(n) for n in range(2001)])
+    prefix = np.concatenate([[0], np.cumsum(mask)])
+    pairs = [(lo, hi) for lo in range(2001) for hi in range(lo, 2001)]
+    for k in range(0, len(pairs), 250_000):
+        chunk = pairs[k:k + 250_000]
+        got = sv.batch_count([p[0] for p in chunk], [p[1] for p in chunk])
+        expect = [int(prefix[hi] - prefix[lo]) for lo, hi in chunk]
+        assert got == expect
+
+
+@pytest.mark.parametrize("lo", [0, 1, 2, 3, 4, 5, 7, 8, 29, 30, 31, 959, 960, 961])
+def test_low_starts_bitmap_and_list(sv, lo):
+    for hi in (lo, lo + 1, lo + 2, lo + 31, lo + 64, lo + 1000, lo + 123_457, 7_000_000):
+        if hi < lo:
+            continue
+        words, c = gpu_bitmap(sv, lo, hi)
+        assert np.array_equal(words, oracle.bitmap(lo, hi)), (lo, hi)
+        assert c == oracle.count(lo, hi)
+        assert sv.count(lo, hi) == c
+        lst = sv.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)
+        assert np.array_equal(lst, oracle.primes(lo, hi)), (lo, hi)
+
+
+def test_every_start_below_1000(sv):
+    # exercises every phase of the segment grid origin (negative wheel bytes included)
+    for lo in range(0, 1000):
+        hi = lo + 3001
+        words, c = gpu_bitmap(sv, lo, hi)
+        assert np.array_equal(words, oracle.bitmap(lo, hi)), lo
+        assert c == oracle.count(lo, hi)
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 9_999_991, 4_294_967_291])
+def test_prime_at_range_edges(sv, p):
+    for lo, hi in ((p, p), (p, p + 1), (p - 1, p), (p - 1, p + 1), (p + 1, p + 2), (0, p), (0, p + 1)):
+        if lo < 0:
+            continue
+        assert sv.count(lo, hi) == oracle.count(lo, hi), (lo, hi)
+        words, _ = gpu_bitmap(sv, lo, hi)
+        assert np.array_equal(words, oracle.bitmap(lo, hi)), (lo, hi)
+
+
+def test_random_ranges_vs_oracle(sv):
+    for lo, hi in random_ranges(60, seed=1205, max_lo=10**12, max_w=2 * 10**7):
+        c = sv.count(lo, hi)
+        assert c == oracle.count(lo, hi), (lo, hi)
+        words, c2 = gpu_bitmap(sv, lo, hi)
+        assert c2 == c
+        assert np.array_equal(words, oracle.bitmap(lo, hi)), (lo, hi)
+
+
+def test_lists_vs_oracle(sv):
+    for lo, hi in random_ranges(12, seed=77, max_lo=2**32 - 10**7, max_w=10**7) + [(2**32 - 10**6, 2**32)]:
+        got = sv.primes(lo, hi).cpu().numpy().view(np.uint32).astype(np.uint64)
+        assert np.array_equal(got, oracle.primes(lo, hi)), (lo, hi)
+    for lo, hi in random_ranges(8, seed=78, max_lo=10**14, max_w=3 * 10**6):
+        got = sv.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, oracle.primes(lo, hi)), (lo, hi)
+
+
+def test_multi_segment_ranges_several_grid_phases(sv):
+    # Ranges spanning many segments, with p^2 crossing segment edges; lo and hi
+    # on and off multiples of 30 and 210, and straddling 2^32.
+    S = sv.get_param(gb.SIEVE_PARAM_SEGMENT_BYTES)
+    span = 30 * S
+    for lo, hi in [(0, 9 * span + 17), (30 * 7, 210 * 100_000), (span - 1, 3 * span + 1),
+                   (2**32 - 5 * span // 2, 2**32 + 5 * span // 2), (10**12 - span, 10**12 + span),
+                   (210 * 10**9, 210 * 10**9 + 4 * span)]:
+        assert sv.count(lo, hi) == oracle.count(lo, hi), (lo, hi)
+        words, _ = gpu_bitmap(sv, lo, hi)
+        assert np.array_equal(words, oracle.bitmap(lo, hi)), (lo, hi)
+
+
+@pytest.mark.parametrize("seg,threads,small,ctas", [(1024, 256, 23, 1), (4096 + 32, 512, 100, 2),
+                                                     (65536, 1024, 65536, 1), (229376, 1024, 7168, 1),
+                                                     (32 * 1001, 256, 2000, 3)])
+def test_launch_parameters_do_not_change_results(seg, threads, small, ctas):
+    with gb.Sieve(10**13) as s:
+        s.set_param(gb.SIEVE_PARAM_SEGMENT_BYTES, seg)
+        s.set_param(gb.SIEVE_PARAM_THREADS, threads)
+        s.set_param(gb.SIEVE_PARAM_SMALL_LIMIT, small)
+        s.set_param(gb.SIEVE_PARAM_CTAS_PER_SM, ctas)
+        for lo, hi in [(0, 10**7), (123_456_789_012, 123_456_789_012 + 3 * 10**6), (5, 40_000)]:
+            assert s.count(lo, hi) == oracle.count(lo, hi)
+            words, _ = s.bitmap(lo, hi)
+            assert np.array_equal(words.cpu().numpy().view(np.uint32), oracle.bitmap(lo, hi))
+
+
+def test_large_lo_against_miller_rabin(sv):
+    lo, hi = 10**14, 10**14 + 60_000
+    got = [int(v) for v in sv.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)]
+    assert got == [n for n in range(lo, hi) if mr_is_prime(n)]
+
+
+def test_additivity_at_scale(sv):
+    for lo, hi in random_ranges(10, seed=9, max_lo=10**14, max_w=10**9):
+        mid = (lo + hi) // 2 + 13
+        mid = min(mid, hi)
+        assert sv.count(lo, mid) + sv.count(mid, hi) == sv.count(lo, hi)
+
+
+def test_count_dev_matches_count(sv):
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for lo, hi in [(0, 10**9), (10**12, 10**12 + 10**8), (7, 8), (100, 100)]:
+        out.fill_(12345)
+        sv.count_dev(lo, hi, out)
+        assert int(out.item()) == sv.count(lo, hi) == oracle.count(lo, hi)
+
+
+def test_errors_and_size_query(sv):
+    with pytest.raises(gb.SieveError) as e:
+        sv.count(10, 5)
+    assert e.value.code == gb.SIEVE_EINVAL
+    with pytest.raises(gb.SieveError) as e:
+        sv.count(0, HI_MAX + 1)
+    assert e.value.code == gb.SIEVE_ERANGE
+    with pytest.raises(gb.SieveError) as e:
+        gb.sieve_list(sv.ctx, 0, 2**32 + 2, None, 0)
+    assert e.value.code == gb.SIEVE_ERANGE
+    n, rc = gb.sieve_list(sv.ctx, 0, 10**6, None, 0)
+    assert rc == gb.SIEVE_ETRUNC and n == PI[10**6]
+    small = torch.zeros(10, dtype=torch.int32, device="cuda")
+    n, rc = gb.sieve_list(sv.ctx, 0, 10**6, small)
+    assert rc == gb.SIEVE_ETRUNC and n == PI[10**6]
+    assert int(small.abs().sum().item()) == 0  # nothing written on ETRUNC
+    bm = torch.zeros(3, dtype=torch.int32, device="cuda")
+    with pytest.raises(gb.SieveError) as e:
+        gb.sieve_bitmap(sv.ctx, 0, 10**4, bm)
+    assert e.value.code == gb.SIEVE_ETRUNC
+    assert sv.count(5, 5) == 0
+    n, rc = gb.sieve_list(sv.ctx, 8, 8, None, 0)
+    assert n == 0 and rc == gb.SIEVE_OK
+
+
+def test_pi_1e12_full_size(sv):
+    # the count-only workload at full size, default launch configuration
+    assert sv.count(0, 10**12) == PI[10**12]
+
+
+def test_range_2p32_bitmap_then_compaction(sv):
+    lo, hi = 0, 1 << 32
+    nw = gb.sieve_bitmap_words(lo, hi)
+    assert nw == 1 << 26
+    bm = torch.empty(nw, dtype=torch.int32, device="cuda")
+    c = gb.sieve_bitmap(sv.ctx, lo, hi, bm)
+    assert c == PI[1 << 32]
+    lst = torch.empty(PI[1 << 32], dtype=torch.int32, device="cuda")
+    n, rc = gb.sieve_compact(sv.ctx, bm, lo, hi, lst)
+    assert rc == gb.SIEVE_OK and n == PI[1 << 32]
+    # properties that hold at any size
+    u = lst.to(torch.int64) & 0xFFFFFFFF
+    assert bool((u[1:] > u[:-1]).all().item())
+    assert int(u[0].item()) == 2 and int(u[-1].item()) == 4_294_967_291
+    # sampled windows against the oracle
+    rng = np.random.default_rng(5)
+    bmh = bm.cpu().numpy().view(np.uint32)
+    for w in rng.integers(0, nw - 1024, 12):
+        a = 64 * int(w)
+        assert np.array_equal(bmh[w:w + 1024], oracle.bitmap(a, a + 64 * 1024)), w
+    uh = u.cpu().numpy()
+    for k in list(rng.integers(0, n - 2000, 4)) + [n - 2000]:
+        k = int(k)
+        window = uh[k:k + 2000].astype(np.uint64)
+        assert np.array_equal(window, oracle.primes(int(window[0]), int(window[-1]) + 1))
+        assert oracle.count(0, int(window[0])) == k  # the rank of the window's first prime
+
+
+def test_batch_4096_intervals(sv):
+    los, his = batch_intervals(4096, seed=1205)
+    counts = sv.batch_count(los, his)
+    # each count equals the single-range call on the same GPU (exact)
+    for i in range(0, 4096, 37):
+        assert counts[i] == sv.count(los[i], his[i]), i
+    # and a seeded sample against the oracle: the narrowest intervals plus random ones
+    order = np.argsort(np.array(his, dtype=np.float64) - np.array(los, dtype=np.float64))
+    sample = list(order[:24]) + list(np.random.default_rng(1).choice(4096, 16, replace=False))
+    for i in sample:
+        i = int(i)
+        if his[i] - los[i] <= 3 * 10**7:
+            assert counts[i] == oracle.count(los[i], his[i]), i
+
+
+def test_batch_with_bitmaps(sv):
+    los, his = batch_intervals(64, seed=11, lo_exp=(3, 13), w_exp=(1, 6))
+    bms = [torch.zeros(max(gb.sieve_bitmap_words(a, b), 1), dtype=torch.int32, device="cuda") if i % 3 else None
+           for i, (a, b) in enumerate(zip(los, his))]
+    counts = sv.batch_count(los, his, bms)
+    for i, (a, b) in enumerate(zip(los, his)):
+        assert counts[i] == oracle.count(a, b), i
+        if bms[i] is not None:
+            nw = gb.sieve_bitmap_words(a, b)
+            assert np.array_equal(bms[i][:nw].cpu().numpy().view(np.uint32), oracle.bitmap(a, b)), i
