@@ -130,6 +130,31 @@ int sieve_compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo,
 int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi,
                       size_t m, uint64_t *counts, uint32_t *const *bitmaps_dev);
 
+/*
+ * Compaction that allocates no device memory, for callers that cannot call
+ * cudaMalloc (code running inside a fixed memory arena, a real-time loop that
+ * must not take the allocator's locks, or a plug-in whose host owns all
+ * device memory).  The paper has no counterpart: this is a deployment aid.
+ *
+ * Same result and *n / cap / SIEVE_ETRUNC contract as sieve_compact, without
+ * a context: it runs on cuda_stream (a cudaStream_t; NULL = the legacy
+ * default stream) of the current device.  Its scratch (per-tile popcounts,
+ * their prefix sums, the total) is a fixed __device__ array of about 384 KiB
+ * inside the library, held by every GPU that loads the library until the
+ * process exits.  Limit: the bitmap may have at most SIEVE_STATIC_MAX_WORDS
+ * words (the whole of [0, 2^32)); larger ranges, or hi > 2^32, return
+ * SIEVE_ERANGE before any GPU work.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls on a device share the one array: calls that
+ * overlap on the GPU (other streams or host threads) race, so serialise them.
+ * The array keeps the last call's contents; every entry is written before it
+ * is read, so nothing needs clearing.  Synchronous, like sieve_compact.
+ */
+#define SIEVE_STATIC_MAX_WORDS (1ull << 26)
+int sieve_compact_static(const uint32_t *bitmap_dev, uint64_t lo, uint64_t hi,
+                         uint32_t *out_dev, size_t cap, uint64_t *n,
+                         void *cuda_stream);
+
 /* Tunable launch parameters (see sieve_set_param / sieve_get_param). */
 #define SIEVE_PARAM_SEGMENT_BYTES 1 /* shared-memory segment, bytes; multiple of 32 */
 #define SIEVE_PARAM_THREADS       2 /* threads per CTA: 256, 512 or 1024 */

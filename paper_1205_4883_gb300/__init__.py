@@ -65,6 +65,7 @@ _SIGS = {
     "sieve_stream": (_vp, [_vp]),
     "sieve_strerror": (ctypes.c_char_p, [_int]),
     "sieve_last_error": (ctypes.c_char_p, [_vp]),
+    "sieve_compact_static": (_int, [_vp, _u64, _u64, _vp, _sz, _pu64, _vp]),
 }
 
 _lib = None
@@ -187,6 +188,17 @@ def sieve_compact(ctx: int, bitmap, lo: int, hi: int, out, cap: Optional[int] = 
     n = _u64()
     rc = load_library().sieve_compact(ctx, _ptr(bitmap), lo, hi, _ptr(out), cap, ctypes.byref(n))
     _check(ctx, rc, allow=(SIEVE_ETRUNC,))
+    return n.value, rc
+
+
+def sieve_compact_static(bitmap, lo: int, hi: int, out, cap: Optional[int] = None, stream: Optional[int] = None):
+    """Compaction with the library's fixed scratch array (no device allocation).
+    Returns (n, rc) with rc SIEVE_OK or SIEVE_ETRUNC; other codes raise."""
+    if cap is None:
+        cap = out.numel() * out.element_size() // 4 if out is not None and not isinstance(out, int) else 0
+    n = _u64()
+    rc = load_library().sieve_compact_static(_ptr(bitmap), lo, hi, _ptr(out), cap, ctypes.byref(n), stream or None)
+    _check(0, rc, allow=(SIEVE_ETRUNC,))
     return n.value, rc
 
 
