@@ -167,6 +167,9 @@ def run_gpu(args):
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     lo, hi = rank * UNITS, (rank + 1) * UNITS
+    if args.hi is not None:  # a smaller slice of the workload (profiling)
+        lo, hi = rank * UNITS + args.lo, rank * UNITS + args.hi
+    units = hi - lo
     sv = gb.Sieve(hi, device=dev)
     stream = torch.cuda.current_stream()
     out = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -204,7 +207,7 @@ def run_gpu(args):
         t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_step = float(t.item())
-    value = ws * UNITS / (ms_step * 1e-3)
+    value = ws * units / (ms_step * 1e-3)
 
     # end to end through the C ABI with the host count (the call a user makes)
     torch.cuda.synchronize()
@@ -232,7 +235,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lo": lo, "hi": hi, "count": expect,
+            "config": {"workload": WORKLOAD if args.hi is None else f"slice [{lo}, {hi}) of the pi(10^12) workload",
+                       "lo": lo, "hi": hi, "count": expect,
                        "segment_bytes": sv.get_param(gb.SIEVE_PARAM_SEGMENT_BYTES),
                        "threads": sv.get_param(gb.SIEVE_PARAM_THREADS),
                        "small_limit": sv.get_param(gb.SIEVE_PARAM_SMALL_LIMIT),
@@ -245,7 +249,7 @@ def run_gpu(args):
                          "peak_basis": f"{n_sms} SMs x 32 lanes/clk x {sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
                          "work_per_launch": clears},
             "clocks": clocks,
-            "e2e": {"value": ws * UNITS / e2e_s, "unit": METRIC, "h2d_bytes_per_step": 72,
+            "e2e": {"value": ws * units / e2e_s, "unit": METRIC, "h2d_bytes_per_step": 72,
                     "d2h_bytes_per_step": 8},
             "gpu_launches": args.steps,
         }
@@ -263,6 +267,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbsieve", choices=["gbsieve", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lo", type=int, default=0, help="with --hi: sieve [lo, hi) of each rank's block instead")
+    ap.add_argument("--hi", type=int, default=None)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -18,6 +18,8 @@ constexpr uint32_t kTilePeriod = 323323u;
 // Largest shared-memory segment a launch may use, bytes (227 KB opt-in limit
 // per CTA minus the kernel's static shared memory).
 constexpr uint32_t kMaxSegmentBytes = 229376u;
+// Small primes whose per-segment residue B0 mod p is cached in shared memory.
+constexpr uint32_t kSmallResidues = 288u;
 // Number of byte-shifted copies of the pattern (one per 16-byte phase).
 constexpr uint32_t kTileCopies = 16u;
 // Index of the first base prime >= 23 in the base-prime array (2, 3, 5, 7,
@@ -53,6 +55,7 @@ struct SieveLaunch {
     const uint32_t *primes;              // base primes, ascending, 2 first
     const uint64_t *magic;               // floor((2^64 - 1) / p) per prime
     uint32_t small_end;                  // primes [8, small_end) crossed warp-cooperatively
+    uint32_t mid_end;                    // primes [small_end, mid_end): per-phase sub-progressions
     const uint8_t *tile;                 // kTileCopies shifted copies of the pattern
     uint64_t tile_stride;                // bytes between copies
     uint32_t seg_bytes;                  // S, multiple of 32, <= kMaxSegmentBytes

@@ -54,7 +54,7 @@ struct sieve_ctx {
     // launch parameters
     uint32_t seg_bytes = kMaxSegmentBytes;
     int threads = 1024;
-    uint32_t small_limit = 7168;
+    uint32_t small_limit = 1792;  // segment bytes / 128
     int ctas_per_sm = 1;
 
     uint64_t device_bytes = 0;
@@ -209,10 +209,15 @@ RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t 
     return r;
 }
 
+uint32_t small_end_for(const std::vector<uint32_t> &primes, uint32_t limit) {
+    uint32_t e = (uint32_t)(std::lower_bound(primes.begin(), primes.end(), limit) - primes.begin());
+    return std::max<uint32_t>(e, kFirstCrossingPrime);
+}
+
 // Run the sieve over ranges h_ranges[0..m) already planned (item_first set
 // here).  Counts land in ctx->d_acc[1..m]; no synchronisation.
-int run_sieve(sieve_ctx *ctx, int mode, const uint32_t *primes_dev, const uint64_t *magic_dev, uint32_t small_end,
-              size_t m) {
+int run_sieve(sieve_ctx *ctx, int mode, const std::vector<uint32_t> &h, const uint32_t *primes_dev,
+              const uint64_t *magic_dev, size_t m) {
     uint64_t items = 0;
     for (size_t i = 0; i < m; ++i) {
         ctx->h_ranges[i].item_first = items;
@@ -228,7 +233,9 @@ int run_sieve(sieve_ctx *ctx, int mode, const uint32_t *primes_dev, const uint64
     L.counts = ctx->d_acc + 1;
     L.primes = primes_dev;
     L.magic = magic_dev;
-    L.small_end = small_end;
+    L.small_end = small_end_for(h, ctx->small_limit);
+    // primes below S / 8 have at least 8 hits per progression in a full segment
+    L.mid_end = std::max<uint32_t>(L.small_end, small_end_for(h, std::max<uint32_t>(ctx->seg_bytes / 8, 23)));
     L.tile = ctx->d_tile;
     L.tile_stride = ctx->tile_stride;
     L.seg_bytes = ctx->seg_bytes;
@@ -239,10 +246,6 @@ int run_sieve(sieve_ctx *ctx, int mode, const uint32_t *primes_dev, const uint64
     return SIEVE_OK;
 }
 
-uint32_t small_end_for(const std::vector<uint32_t> &primes, uint32_t limit) {
-    uint32_t e = (uint32_t)(std::lower_bound(primes.begin(), primes.end(), limit) - primes.begin());
-    return std::max<uint32_t>(e, kFirstCrossingPrime);
-}
 
 // Compact the odd-only bitmap of [lo, hi) at bitmap_dev into out_dev (uint32 or
 // uint64 values).  *n = number of primes (2 included).
@@ -287,7 +290,7 @@ int primes_upto(sieve_ctx *ctx, uint64_t limit, const std::vector<uint32_t> &h, 
     rc = ensure_bitmap(ctx, bitmap_words_of(0, hi));
     if (rc) return rc;
     ctx->h_ranges[0] = plan_range(h, 0, hi, ctx->seg_bytes, kModeBitmap, ctx->d_bitmap);
-    rc = run_sieve(ctx, kModeBitmap, primes_dev, magic_dev, small_end_for(h, ctx->small_limit), 1);
+    rc = run_sieve(ctx, kModeBitmap, h, primes_dev, magic_dev, 1);
     if (rc) return rc;
     uint64_t n = 0;
     rc = compact(ctx, ctx->d_bitmap, 0, hi, nullptr, 0, &n, 0);
@@ -375,7 +378,7 @@ int sieve_bitmap_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_de
     int rc = ensure_ranges(ctx, 1);
     if (rc) return rc;
     ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeBitmap, out_dev);
-    rc = run_sieve(ctx, kModeBitmap, ctx->d_primes, ctx->d_magic, small_end_for(ctx->h_primes, ctx->small_limit), 1);
+    rc = run_sieve(ctx, kModeBitmap, ctx->h_primes, ctx->d_primes, ctx->d_magic, 1);
     if (rc) return rc;
     CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                        ctx->stream));
@@ -474,7 +477,7 @@ int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count) {
     rc = ensure_ranges(ctx, 1);
     if (rc) return rc;
     ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeCount, nullptr);
-    rc = run_sieve(ctx, kModeCount, ctx->d_primes, ctx->d_magic, small_end_for(ctx->h_primes, ctx->small_limit), 1);
+    rc = run_sieve(ctx, kModeCount, ctx->h_primes, ctx->d_primes, ctx->d_magic, 1);
     if (rc) return rc;
     CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                        ctx->stream));
@@ -491,7 +494,7 @@ int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_de
     rc = ensure_ranges(ctx, 1);
     if (rc) return rc;
     ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeCount, nullptr);
-    rc = run_sieve(ctx, kModeCount, ctx->d_primes, ctx->d_magic, small_end_for(ctx->h_primes, ctx->small_limit), 1);
+    rc = run_sieve(ctx, kModeCount, ctx->h_primes, ctx->d_primes, ctx->d_magic, 1);
     if (rc) return rc;
     CK(cudaMemcpyAsync(count_dev, ctx->d_acc + 1, sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream));
     return SIEVE_OK;
@@ -567,7 +570,7 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, si
         uint32_t *bm = bitmaps_dev ? bitmaps_dev[i] : nullptr;
         ctx->h_ranges[i] = plan_range(ctx->h_primes, lo[i], hi[i], ctx->seg_bytes, mode, bm);
     }
-    rc = run_sieve(ctx, mode, ctx->d_primes, ctx->d_magic, small_end_for(ctx->h_primes, ctx->small_limit), m);
+    rc = run_sieve(ctx, mode, ctx->h_primes, ctx->d_primes, ctx->d_magic, m);
     if (rc) return rc;
     CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, m * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                        ctx->stream));

@@ -73,33 +73,53 @@ __device__ __forceinline__ void clear_bit(uint32_t *seg32, uint32_t off, uint32_
     atomicAnd(&seg32[off >> 2], ~(1u << (((off & 3u) << 3) | bit)));
 }
 
-// First byte offset (relative to B0) of progression j of prime p in a segment
-// starting at wheel byte B0; Bc = max(B0, 0), R = Bc mod p.  Returns a value
-// >= L when the progression misses the first L bytes.
-struct ClassStart {
-    uint32_t off;
-    uint32_t bit;
-};
+// Byte offset (relative to the segment start B0) of the first multiple of p
+// in progression j, i.e. of the first p m >= max(p^2, 30 B0) with
+// m = r_j (mod 30); R = max(B0, 0) mod p.  In wheel bytes the progression is
+// c_j + p q with c_j = floor(p r_j / 30) = pq r_j + floor(r_c r_j / 30), so the
+// offset is (c_j - R) mod p -- unless the segment starts before p^2 ("early",
+// always the case when B0 < 0), when the start is clamped to the byte of the
+// first multiple with m >= p.  Values >= L mean "no hit in this segment".
+__device__ __forceinline__ uint32_t class_off(const WheelTables &t, uint32_t p, uint32_t pq, uint32_t pc, int j,
+                                              uint32_t R, int64_t B0, bool early, uint32_t L) {
+    const uint32_t rj = c_res[j];
+    const uint32_t cj = pq * rj + t.adj[pc * 8 + j];
+    uint32_t d = cj - R;
+    if ((int32_t)d < 0) d += p;
+    if (!early) return d;
+    const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
+    uint64_t start = Bc + d;
+    const uint64_t q0 = p > rj ? (uint64_t)((p - rj + 29) / 30) : 0;  // m = 30 q + r_j >= p
+    const uint64_t bmin = (uint64_t)p * q0 + cj;
+    if (bmin > start) start = bmin;
+    const int64_t off = (int64_t)start - B0;
+    return off < (int64_t)L ? (uint32_t)off : L;
+}
 
-__device__ __forceinline__ ClassStart class_start(const WheelTables &t, uint32_t p, uint32_t pq, uint32_t pc,
-                                                  int j, uint32_t R, int64_t B0, uint64_t Bc, bool early,
-                                                  uint32_t L) {
-    uint32_t cj = pq * c_res[j] + t.adj[pc * 8 + j];
-    int32_t d = (int32_t)(cj - R);
-    if (d < 0) d += (int32_t)p;
-    uint64_t start = Bc + (uint32_t)d;
-    if (early) {
-        // multiples p m with m < p are left alone: m = 30 q + r_j >= p
-        uint32_t rj = c_res[j];
-        uint64_t q0 = p > rj ? (uint64_t)((p - rj + 29) / 30) : 0;
-        uint64_t bmin = (uint64_t)p * q0 + cj;
-        if (bmin > start) start = bmin;
+// All eight progressions of p in a segment that starts before p^2 (or before
+// integer 0): the rare case, kept out of line so the common path stays short.
+__device__ __noinline__ void cross_prime_early(const WheelTables &t, uint32_t *seg32, uint32_t p, uint32_t pq,
+                                               uint32_t pc, uint32_t R, int64_t B0, uint32_t L) {
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t off = class_off(t, p, pq, pc, j, R, B0, true, L);
+        const uint32_t bit = t.bit[pc * 8 + j];
+        for (uint32_t o = off; o < L; o += p) clear_bit(seg32, o, bit);
     }
-    int64_t off = (int64_t)start - B0;
-    ClassStart cs;
-    cs.off = off < (int64_t)L ? (uint32_t)off : L;
-    cs.bit = t.bit[pc * 8 + j];
-    return cs;
+}
+
+// True when the segment starting at wheel byte B0 (Bc = max(B0, 0)) may begin
+// before some progression's first allowed multiple p m, m >= p: those bytes are
+// all below p^2 / 30 + 2 p, so 30 Bc >= p^2 + 60 p rules it out.
+__device__ __forceinline__ bool is_early(int64_t B0, uint64_t Bc, uint32_t p) {
+    return B0 < 0 || 30ull * Bc < (uint64_t)p * p + 60ull * p;
+}
+
+// Inverse of an odd p modulo 128 (Newton steps: p is its own inverse mod 8).
+__device__ __forceinline__ uint32_t inv_mod128(uint32_t p) {
+    uint32_t x = p;
+    x *= 2u - p * x;  // mod 64
+    x *= 2u - p * x;  // mod 4096
+    return x & 127u;
 }
 
 // Bits of wheel word w (4 bytes at integers base .. base + 119, base relative
@@ -130,6 +150,8 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(SieveLaunch P) {
     __shared__ uint32_t s_range;
     __shared__ uint32_t s_small_next;
     __shared__ unsigned long long s_red[32];
+    __shared__ uint32_t s_R[kSmallResidues];  // B0 mod p for the first small primes
+    __shared__ uint32_t s_nseg;                 // base primes with p^2 below the segment end
 
     init_tables(tab);
     const int tid = threadIdx.x, lane = tid & 31;
@@ -164,9 +186,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(SieveLaunch P) {
             need = (need + 31) & ~(int64_t)31;
             L = need < (int64_t)S ? (uint32_t)need : S;
         }
-        const uint32_t n_use = rd.n_use;
-        const uint32_t small_end = P.small_end < n_use ? P.small_end : n_use;
-        const uint32_t n_small8 = (small_end > kFirstCrossingPrime ? small_end - kFirstCrossingPrime : 0) * 8;
+        const uint32_t n_range = rd.n_use;
 
         // 1. pre-sieved pattern -> shared memory (16-byte aligned copy)
         {
@@ -176,23 +196,109 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(SieveLaunch P) {
             const uint4 *src = reinterpret_cast<const uint4 *>(P.tile + k * P.tile_stride + ((uint32_t)ph - k));
             for (uint32_t i = tid; i < L / 16; i += blockDim.x) smem4[i] = __ldg(src + i);
         }
+        // primes with p^2 >= the segment's end have no multiple to cross here:
+        // warp 0 finds how many base primes remain (32-way search)
+        if (tid < 32) {
+            const int64_t seg_end = base_int + 30 * (int64_t)L;
+            const uint64_t E = (uint64_t)(seg_end < (int64_t)rd.hi ? seg_end : (int64_t)rd.hi);
+            uint32_t a = 0, b = n_range;
+            while (b - a > 32) {
+                const uint32_t step = (b - a + 31) / 32, idx = a + (uint32_t)lane * step;
+                bool ok = false;
+                if (idx < b) {
+                    const uint64_t q = __ldg(P.primes + idx);
+                    ok = q * q < E;
+                }
+                const int c = __popc(__ballot_sync(0xffffffffu, ok));
+                if (c == 0) {
+                    b = a;
+                    break;
+                }
+                const uint32_t na = a + (uint32_t)(c - 1) * step + 1, nb = a + (uint32_t)c * step;
+                a = na;
+                b = nb < b ? nb : b;
+            }
+            bool ok = false;
+            if (a + lane < b) {
+                const uint64_t q = __ldg(P.primes + a + lane);
+                ok = q * q < E;
+            }
+            const uint32_t n = a + __popc(__ballot_sync(0xffffffffu, ok));
+            if (lane == 0) s_nseg = n;
+        }
+        {
+            const uint32_t se = P.small_end < n_range ? P.small_end : n_range;
+            const uint32_t nr = se > kFirstCrossingPrime ? se - kFirstCrossingPrime : 0;
+            for (uint32_t t = tid; t < nr && t < kSmallResidues; t += blockDim.x)
+                s_R[t] = mod_barrett(Bc, __ldg(P.primes + kFirstCrossingPrime + t),
+                                     __ldg(P.magic + kFirstCrossingPrime + t));
+        }
         __syncthreads();
+        const uint32_t n_use = s_nseg;
+        const uint32_t small_end = P.small_end < n_use ? P.small_end : n_use;
+        const uint32_t n_small8 = (small_end > kFirstCrossingPrime ? small_end - kFirstCrossingPrime : 0) * 8;
 
-        // 2a. one thread per prime for primes [small_end, n_use)
-        for (uint32_t i = P.small_end + tid; i < n_use; i += blockDim.x) {
-            const uint32_t p = __ldg(P.primes + i);
-            const uint64_t M = __ldg(P.magic + i);
+        // 2a. medium primes [small_end, mid_end): one lane per prime, the warp
+        //     taking 32 consecutive primes at a time (warp-uniform loop, so
+        //     the lanes can be re-converged after every sub-loop).  Each of the
+        //     eight progressions (stride p bytes) is split into four
+        //     sub-progressions of stride 4 p bytes = p words, one per byte
+        //     phase, each crossed with one fixed mask.
+        const uint32_t mid_end = P.mid_end < n_use ? P.mid_end : n_use;
+        const uint32_t Lw = L >> 2;
+        for (uint32_t base = P.small_end + (tid & ~31u); base < mid_end; base += blockDim.x) {
+            const uint32_t i = base + lane;
+            const bool valid = i < mid_end;
+            const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
+            const uint64_t M = valid ? __ldg(P.magic + i) : ~0ull;
             const uint32_t R = mod_barrett(Bc, p, M);
-            const uint32_t pq = p / 30, pc = tab.cls[p - pq * 30];
-            const bool early = Bc < ((uint64_t)p * p) / 30 + 2ull * p + 2ull;
+            const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
+            const bool early = valid && is_early(B0, Bc, p);
+            if (early) cross_prime_early(tab, seg32, p, pq, pc, R, B0, L);
+            __syncwarp();
+            const uint32_t lw = (valid && !early) ? Lw : 0u;  // fast path only for the others
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                ClassStart cs = class_start(tab, p, pq, pc, j, R, B0, Bc, early, L);
-                for (uint32_t o = cs.off; o < L; o += p) clear_bit(seg32, o, cs.bit);
+                const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, false, L);
+                const uint32_t bit = tab.bit[pc * 8 + j];
+#pragma unroll
+                for (uint32_t ph = 0; ph < 4; ++ph) {
+                    // p^-1 = p (mod 4), so off + k p = ph (mod 4) for k = (ph - off) p mod 4
+                    const uint32_t o = off + (((ph - off) * p) & 3u) * p;
+                    const uint32_t mask = ~(1u << (8u * ph + bit));
+                    for (uint32_t w = o >> 2; w < lw; w += p) atomicAnd(&seg32[w], mask);
+                }
+                __syncwarp();
             }
         }
-        // 2b. warp-cooperative: one (prime, class) progression per warp, lanes
-        //     striding by 32 p; items in decreasing order of hits, taken dynamically
+        // 2a'. large primes [mid_end, n_use): one lane per prime, at most a
+        //      few hits per progression, crossed directly
+        for (uint32_t base = mid_end + (tid & ~31u); base < n_use; base += blockDim.x) {
+            const uint32_t i = base + lane;
+            const bool valid = i < n_use;
+            const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
+            const uint64_t M = valid ? __ldg(P.magic + i) : ~0ull;
+            const uint32_t R = mod_barrett(Bc, p, M);
+            const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
+            const bool early = valid && is_early(B0, Bc, p);
+            if (early) cross_prime_early(tab, seg32, p, pq, pc, R, B0, L);
+            __syncwarp();
+            const uint32_t l = (valid && !early) ? L : 0u;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, false, L);
+                const uint32_t bit = tab.bit[pc * 8 + j];
+                for (uint32_t o = off; o < l; o += p) clear_bit(seg32, o, bit);
+            }
+            __syncwarp();
+        }
+        // 2b. small primes [8, small_end): one (prime, class) progression per
+        //     warp, taken dynamically in decreasing order of work.  The
+        //     progression (stride p bytes) is split into 128 sub-progressions of
+        //     stride 128 p: lane l takes the four whose bytes are 4 l + q
+        //     (mod 128), q = 0..3.  Every lane then always writes bank l of the
+        //     segment with one fixed bit mask, so a warp's 32 atomics never share
+        //     a bank and need no per-hit mask arithmetic.
         for (;;) {
             uint32_t k = 0;
             if (lane == 0) k = atomicAdd(&s_small_next, 1u);
@@ -201,23 +307,22 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(SieveLaunch P) {
             const uint32_t i = kFirstCrossingPrime + (k >> 3);
             const int j = (int)(k & 7);
             const uint32_t p = __ldg(P.primes + i);
-            const uint64_t M = __ldg(P.magic + i);
-            const uint32_t R = mod_barrett(Bc, p, M);
+            const uint32_t t = i - kFirstCrossingPrime;
+            const uint32_t R = t < kSmallResidues ? s_R[t] : mod_barrett(Bc, p, __ldg(P.magic + i));
             const uint32_t pq = p / 30, pc = tab.cls[p - pq * 30];
-            const bool early = Bc < ((uint64_t)p * p) / 30 + 2ull * p + 2ull;
-            ClassStart cs;
-            switch (j) {  // keep j a compile-time index into c_res
-                case 0: cs = class_start(tab, p, pq, pc, 0, R, B0, Bc, early, L); break;
-                case 1: cs = class_start(tab, p, pq, pc, 1, R, B0, Bc, early, L); break;
-                case 2: cs = class_start(tab, p, pq, pc, 2, R, B0, Bc, early, L); break;
-                case 3: cs = class_start(tab, p, pq, pc, 3, R, B0, Bc, early, L); break;
-                case 4: cs = class_start(tab, p, pq, pc, 4, R, B0, Bc, early, L); break;
-                case 5: cs = class_start(tab, p, pq, pc, 5, R, B0, Bc, early, L); break;
-                case 6: cs = class_start(tab, p, pq, pc, 6, R, B0, Bc, early, L); break;
-                default: cs = class_start(tab, p, pq, pc, 7, R, B0, Bc, early, L); break;
+            const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, is_early(B0, Bc, p), L);
+            if (off >= L) continue;
+            const uint32_t bit = tab.bit[pc * 8 + j];
+            const uint32_t pinv = inv_mod128(p);
+            const uint32_t Lw = L >> 2, wstep = 32u * p;  // 128 p bytes = 32 p words
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {
+                const uint32_t kappa = ((4u * (uint32_t)lane + q - off) * pinv) & 127u;
+                const uint32_t o = off + kappa * p;  // = 4 lane + q (mod 128)
+                const uint32_t mask = ~(1u << (8u * q + bit));
+#pragma unroll 4
+                for (uint32_t w = o >> 2; w < Lw; w += wstep) atomicAnd(&seg32[w], mask);
             }
-            const uint32_t step = 32u * p;
-            for (uint32_t o = cs.off + (uint32_t)lane * p; o < L; o += step) clear_bit(seg32, o, cs.bit);
         }
         __syncthreads();
 
