@@ -160,6 +160,9 @@ int sieve_compact_static(const uint32_t *bitmap_dev, uint64_t lo, uint64_t hi,
 #define SIEVE_PARAM_THREADS       2 /* threads per CTA: 256, 512 or 1024 */
 #define SIEVE_PARAM_SMALL_LIMIT   3 /* primes below this are crossed warp-cooperatively */
 #define SIEVE_PARAM_CTAS_PER_SM   4 /* persistent CTAs per SM */
+#define SIEVE_PARAM_CHUNK_SEGMENTS 5 /* consecutive segments per work item (1..64) */
+#define SIEVE_PARAM_BUCKET_LIMIT  6 /* primes >= this go through bucket lists; 0 = segment bytes;
+                                       default 2^62 (off: direct crossing measured faster) */
 
 /* Set a launch parameter for later calls on ctx (SIEVE_EINVAL if out of range). */
 int sieve_set_param(sieve_ctx *ctx, int param, int64_t value);

@@ -30,6 +30,8 @@ SIEVE_PARAM_SEGMENT_BYTES = 1
 SIEVE_PARAM_THREADS = 2
 SIEVE_PARAM_SMALL_LIMIT = 3
 SIEVE_PARAM_CTAS_PER_SM = 4
+SIEVE_PARAM_CHUNK_SEGMENTS = 5
+SIEVE_PARAM_BUCKET_LIMIT = 6
 
 _u64 = ctypes.c_uint64
 _i64 = ctypes.c_int64

@@ -18,6 +18,8 @@ constexpr uint32_t kTilePeriod = 323323u;
 // Largest shared-memory segment a launch may use, bytes (227 KB opt-in limit
 // per CTA minus the kernel's static shared memory).
 constexpr uint32_t kMaxSegmentBytes = 229376u;
+// Most segments one work item (a chunk) may hold; bucket lists are per segment of a chunk.
+constexpr uint32_t kMaxChunkSegments = 64u;
 // Small primes whose per-segment residue B0 mod p is cached in shared memory.
 constexpr uint32_t kSmallResidues = 288u;
 // Number of byte-shifted copies of the pattern (one per 16-byte phase).
@@ -34,7 +36,7 @@ constexpr uint32_t kFirstCrossingPrime = 8u;
 struct RangeDesc {
     int64_t Bbase;          // wheel byte of segment 0
     uint64_t lo, hi;        // the half-open range
-    uint64_t item_first;    // launch-wide index of this range's segment 0
+    uint64_t item_first;    // launch-wide index of this range's first chunk
     uint64_t nseg;          // segments in this range
     uint32_t *bitmap;       // odd-only output (bitmap mode); null: count only
     uint64_t bitmap_words;  // words of the odd-only bitmap of [lo, hi)
@@ -49,13 +51,18 @@ enum SieveMode : int { kModeCount = 0, kModeBitmap = 1 };
 struct SieveLaunch {
     const RangeDesc *ranges;
     uint32_t n_ranges;
-    uint64_t n_items;                    // total segments over all ranges
+    uint64_t n_items;                    // total chunks over all ranges
     unsigned long long *item_counter;    // zeroed before the launch
     unsigned long long *counts;          // one per range, zeroed before the launch
     const uint32_t *primes;              // base primes, ascending, 2 first
     const uint64_t *magic;               // floor((2^64 - 1) / p) per prime
     uint32_t small_end;                  // primes [8, small_end) crossed warp-cooperatively
     uint32_t mid_end;                    // primes [small_end, mid_end): per-phase sub-progressions
+    uint32_t bucket_first;               // primes [bucket_first, ...) go through the bucket lists
+    uint32_t chunk_segs;                 // segments per work item, <= kMaxChunkSegments
+    uint32_t *buckets;                   // grid x chunk_segs x bucket_cap entries
+    uint32_t bucket_cap;                 // entries per segment list
+    unsigned *overflow;                  // set to 1 if a list overflowed (zeroed before the launch)
     const uint8_t *tile;                 // kTileCopies shifted copies of the pattern
     uint64_t tile_stride;                // bytes between copies
     uint32_t seg_bytes;                  // S, multiple of 32, <= kMaxSegmentBytes
@@ -81,5 +88,8 @@ cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t 
                         uint64_t ntiles, uint64_t o0, uint32_t base_index, void *out,
                         int out64, int grid, cudaStream_t stream);
 cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream);
+// *out = *count, or UINT64_MAX when *overflow is set.
+cudaError_t launch_finalize_count(const unsigned long long *count, const unsigned *overflow, uint64_t *out,
+                                  cudaStream_t stream);
 
 }  // namespace gbs

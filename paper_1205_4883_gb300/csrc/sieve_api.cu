@@ -51,11 +51,18 @@ struct sieve_ctx {
     uint64_t *d_tile_offsets = nullptr;
     size_t tiles_cap = 0;
 
+    // bucket lists for the large primes (grid x chunk x cap entries)
+    uint32_t *d_buckets = nullptr;
+    size_t buckets_entries = 0;
+    double bucket_slack = 1.15;  // capacity = slack x expected hits + 4096, raised on overflow
+
     // launch parameters
     uint32_t seg_bytes = kMaxSegmentBytes;
     int threads = 1024;
     uint32_t small_limit = 1792;  // segment bytes / 128
     int ctas_per_sm = 1;
+    uint32_t chunk_segs = 16;
+    uint64_t bucket_limit = 1ull << 62;  // primes >= this use the bucket lists; 0: the segment size
 
     uint64_t device_bytes = 0;
     std::string last_error;
@@ -141,7 +148,7 @@ int ensure_ranges(sieve_ctx *ctx, size_t m) {
     if (m <= ctx->ranges_cap) return SIEVE_OK;
     size_t cap = std::max<size_t>(m, 64);
     dev_free(ctx, ctx->d_ranges, ctx->ranges_cap);
-    dev_free(ctx, ctx->d_acc, ctx->acc_cap + 1);
+    dev_free(ctx, ctx->d_acc, ctx->acc_cap + 2);
     if (ctx->h_ranges) cudaFreeHost(ctx->h_ranges);
     if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
     ctx->h_ranges = nullptr;
@@ -149,10 +156,10 @@ int ensure_ranges(sieve_ctx *ctx, size_t m) {
     ctx->ranges_cap = ctx->acc_cap = 0;
     int rc = dev_alloc(ctx, &ctx->d_ranges, cap);
     if (rc) return rc;
-    rc = dev_alloc(ctx, &ctx->d_acc, cap + 1);
+    rc = dev_alloc(ctx, &ctx->d_acc, cap + 2);
     if (rc) return rc;
     CK(cudaMallocHost(&ctx->h_ranges, cap * sizeof(RangeDesc)));
-    CK(cudaMallocHost(&ctx->h_acc, (cap + 1) * sizeof(unsigned long long)));
+    CK(cudaMallocHost(&ctx->h_acc, (cap + 2) * sizeof(unsigned long long)));
     ctx->ranges_cap = ctx->acc_cap = cap;
     return SIEVE_OK;
 }
@@ -215,37 +222,106 @@ uint32_t small_end_for(const std::vector<uint32_t> &primes, uint32_t limit) {
 }
 
 // Run the sieve over ranges h_ranges[0..m) already planned (item_first set
-// here).  Counts land in ctx->d_acc[1..m]; no synchronisation.
+// here).  Layout of ctx->d_acc: [0] work counter, [1..m] per-range counts,
+// [m+1] bucket-overflow flag.  No synchronisation.
 int run_sieve(sieve_ctx *ctx, int mode, const std::vector<uint32_t> &h, const uint32_t *primes_dev,
               const uint64_t *magic_dev, size_t m) {
+    uint64_t segs = 0;
+    uint32_t nmax = 0;
+    for (size_t i = 0; i < m; ++i) {
+        segs += ctx->h_ranges[i].nseg;
+        if (ctx->h_ranges[i].nseg) nmax = std::max(nmax, ctx->h_ranges[i].n_use);
+    }
+    const uint64_t grid_max = (uint64_t)ctx->num_sms * ctx->ctas_per_sm;
+    const uint32_t mid_end = std::max<uint32_t>(small_end_for(h, ctx->small_limit),
+                                                small_end_for(h, std::max<uint32_t>(ctx->seg_bytes / 8, 23)));
+    const uint64_t blim = ctx->bucket_limit ? ctx->bucket_limit : ctx->seg_bytes;
+    const uint32_t bfirst = std::max(blim > 0xffffffffull ? (uint32_t)h.size() : small_end_for(h, (uint32_t)blim),
+                                     mid_end);
+    const bool buckets = bfirst < nmax;
+    // Chunks (several segments per work item) only pay off with bucket lists;
+    // keep at least 4 items per CTA so the last wave stays short.
+    uint32_t C = 1;
+    if (buckets) {
+        C = ctx->chunk_segs;
+        while (C > 1 && segs / C < 4 * grid_max) C /= 2;
+    }
     uint64_t items = 0;
     for (size_t i = 0; i < m; ++i) {
         ctx->h_ranges[i].item_first = items;
-        items += ctx->h_ranges[i].nseg;
+        items += (ctx->h_ranges[i].nseg + C - 1) / C;
     }
     CK(cudaMemcpyAsync(ctx->d_ranges, ctx->h_ranges, m * sizeof(RangeDesc), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_acc, 0, (m + 1) * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_acc, 0, (m + 2) * sizeof(unsigned long long), ctx->stream));
     SieveLaunch L;
+    std::memset(&L, 0, sizeof L);
     L.ranges = ctx->d_ranges;
     L.n_ranges = (uint32_t)m;
     L.n_items = items;
     L.item_counter = ctx->d_acc;
     L.counts = ctx->d_acc + 1;
+    L.overflow = reinterpret_cast<unsigned *>(ctx->d_acc + m + 1);
     L.primes = primes_dev;
     L.magic = magic_dev;
-    L.small_end = small_end_for(h, ctx->small_limit);
-    // primes below S / 8 have at least 8 hits per progression in a full segment
-    L.mid_end = std::max<uint32_t>(L.small_end, small_end_for(h, std::max<uint32_t>(ctx->seg_bytes / 8, 23)));
     L.tile = ctx->d_tile;
     L.tile_stride = ctx->tile_stride;
     L.seg_bytes = ctx->seg_bytes;
     L.threads = ctx->threads;
-    uint64_t grid = (uint64_t)ctx->num_sms * ctx->ctas_per_sm;
-    L.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(grid, items));
+    L.chunk_segs = C;
+    L.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(grid_max, items));
+    L.small_end = small_end_for(h, ctx->small_limit);
+    // primes below S / 8 have at least 8 hits per progression in a full segment
+    L.mid_end = mid_end;
+    // primes from the bucket limit up go through the per-segment bucket lists
+    L.bucket_first = 0xffffffffu;
+    if (buckets) {
+        // expected hits per full segment: 8 S / p per bucket prime (one per wheel class
+        // with probability S / p); the list capacity is that with a margin
+        double e = 0;
+        for (uint32_t i = bfirst; i < nmax; ++i) e += 8.0 * ctx->seg_bytes / h[i];
+        uint64_t cap = (uint64_t)(ctx->bucket_slack * e) + 4096;
+        cap = (cap + 31) & ~31ull;
+        const size_t need = (size_t)L.grid * C * cap;
+        if (need > ctx->buckets_entries) {
+            dev_free(ctx, ctx->d_buckets, ctx->buckets_entries);
+            ctx->buckets_entries = 0;
+            int rc = dev_alloc(ctx, &ctx->d_buckets, need);
+            if (rc) return rc;
+            ctx->buckets_entries = need;
+        }
+        L.bucket_first = bfirst;
+        L.buckets = ctx->d_buckets;
+        L.bucket_cap = (uint32_t)cap;
+    }
     CK(launch_sieve(mode, L, ctx->stream));
     return SIEVE_OK;
 }
 
+// Copy the m counts and the overflow flag to ctx->h_acc and wait.  Returns 1
+// if a bucket list overflowed (the results are then invalid), 0 if not.
+int finish_sieve(sieve_ctx *ctx, size_t m, int *overflowed) {
+    CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, (m + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *overflowed = (ctx->h_acc[m] & 0xffffffffull) != 0;
+    return SIEVE_OK;
+}
+
+// run_sieve + finish_sieve, re-running with larger bucket lists if one
+// overflowed (never expected: the margin is far above the spread of the hit
+// counts).  Counts are left in ctx->h_acc[0..m).
+int run_sieve_sync(sieve_ctx *ctx, int mode, size_t m) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        int rc = run_sieve(ctx, mode, ctx->h_primes, ctx->d_primes, ctx->d_magic, m);
+        if (rc) return rc;
+        int of = 0;
+        rc = finish_sieve(ctx, m, &of);
+        if (rc) return rc;
+        if (!of) return SIEVE_OK;
+        ctx->bucket_slack *= 2;
+    }
+    return fail(ctx, SIEVE_EDEVICE, "bucket lists overflowed repeatedly");
+}
 
 // Compact the odd-only bitmap of [lo, hi) at bitmap_dev into out_dev (uint32 or
 // uint64 values).  *n = number of primes (2 included).
@@ -290,8 +366,16 @@ int primes_upto(sieve_ctx *ctx, uint64_t limit, const std::vector<uint32_t> &h, 
     rc = ensure_bitmap(ctx, bitmap_words_of(0, hi));
     if (rc) return rc;
     ctx->h_ranges[0] = plan_range(h, 0, hi, ctx->seg_bytes, kModeBitmap, ctx->d_bitmap);
-    rc = run_sieve(ctx, kModeBitmap, h, primes_dev, magic_dev, 1);
-    if (rc) return rc;
+    for (int attempt = 0;; ++attempt) {
+        rc = run_sieve(ctx, kModeBitmap, h, primes_dev, magic_dev, 1);
+        if (rc) return rc;
+        int of = 0;
+        rc = finish_sieve(ctx, 1, &of);
+        if (rc) return rc;
+        if (!of) break;
+        if (attempt == 3) return fail(ctx, SIEVE_EDEVICE, "bucket lists overflowed repeatedly");
+        ctx->bucket_slack *= 2;
+    }
     uint64_t n = 0;
     rc = compact(ctx, ctx->d_bitmap, 0, hi, nullptr, 0, &n, 0);
     if (rc != SIEVE_ETRUNC && rc != SIEVE_OK) return rc;
@@ -378,11 +462,8 @@ int sieve_bitmap_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_de
     int rc = ensure_ranges(ctx, 1);
     if (rc) return rc;
     ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeBitmap, out_dev);
-    rc = run_sieve(ctx, kModeBitmap, ctx->h_primes, ctx->d_primes, ctx->d_magic, 1);
+    rc = run_sieve_sync(ctx, kModeBitmap, 1);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
     if (count) *count = ctx->h_acc[0];
     return SIEVE_OK;
 }
@@ -459,6 +540,7 @@ void sieve_destroy(sieve_ctx *ctx) {
     cudaFree(ctx->d_bitmap);
     cudaFree(ctx->d_tile_counts);
     cudaFree(ctx->d_tile_offsets);
+    cudaFree(ctx->d_buckets);
     if (ctx->h_ranges) cudaFreeHost(ctx->h_ranges);
     if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -477,11 +559,8 @@ int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count) {
     rc = ensure_ranges(ctx, 1);
     if (rc) return rc;
     ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeCount, nullptr);
-    rc = run_sieve(ctx, kModeCount, ctx->h_primes, ctx->d_primes, ctx->d_magic, 1);
+    rc = run_sieve_sync(ctx, kModeCount, 1);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
     *count = ctx->h_acc[0];
     return SIEVE_OK;
 }
@@ -496,7 +575,9 @@ int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_de
     ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeCount, nullptr);
     rc = run_sieve(ctx, kModeCount, ctx->h_primes, ctx->d_primes, ctx->d_magic, 1);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(count_dev, ctx->d_acc + 1, sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream));
+    // the count, or UINT64_MAX if a bucket list overflowed
+    CK(launch_finalize_count(ctx->d_acc + 1, reinterpret_cast<const unsigned *>(ctx->d_acc + 2), count_dev,
+                             ctx->stream));
     return SIEVE_OK;
 }
 
@@ -570,11 +651,8 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, si
         uint32_t *bm = bitmaps_dev ? bitmaps_dev[i] : nullptr;
         ctx->h_ranges[i] = plan_range(ctx->h_primes, lo[i], hi[i], ctx->seg_bytes, mode, bm);
     }
-    rc = run_sieve(ctx, mode, ctx->h_primes, ctx->d_primes, ctx->d_magic, m);
+    rc = run_sieve_sync(ctx, mode, m);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, m * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
     for (size_t i = 0; i < m; ++i) counts[i] = ctx->h_acc[i];
     return SIEVE_OK;
 }
@@ -598,6 +676,14 @@ int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
             if (v < 1 || v > 8) return fail(ctx, SIEVE_EINVAL, "ctas per sm");
             ctx->ctas_per_sm = (int)v;
             return SIEVE_OK;
+        case SIEVE_PARAM_CHUNK_SEGMENTS:
+            if (v < 1 || v > (int64_t)kMaxChunkSegments) return fail(ctx, SIEVE_EINVAL, "chunk segments");
+            ctx->chunk_segs = (uint32_t)v;
+            return SIEVE_OK;
+        case SIEVE_PARAM_BUCKET_LIMIT:
+            if (v < 0) return fail(ctx, SIEVE_EINVAL, "bucket limit");
+            ctx->bucket_limit = (uint64_t)v;
+            return SIEVE_OK;
         default:
             return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
@@ -610,6 +696,8 @@ int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
         case SIEVE_PARAM_THREADS: *v = ctx->threads; return SIEVE_OK;
         case SIEVE_PARAM_SMALL_LIMIT: *v = ctx->small_limit; return SIEVE_OK;
         case SIEVE_PARAM_CTAS_PER_SM: *v = ctx->ctas_per_sm; return SIEVE_OK;
+        case SIEVE_PARAM_CHUNK_SEGMENTS: *v = ctx->chunk_segs; return SIEVE_OK;
+        case SIEVE_PARAM_BUCKET_LIMIT: *v = (int64_t)ctx->bucket_limit; return SIEVE_OK;
         default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
 }

@@ -31,7 +31,20 @@ struct WheelTables {
     uint8_t adj[64];       // [class of p][j]: floor(r_c * r_j / 30)
     uint8_t bit[64];       // [class of p][j]: wheel bit of (r_c * r_j) mod 30
     uint8_t cls[32];       // residue mod 30 -> wheel class (0xff if not coprime)
+    uint64_t adj40[8];     // [class of p]: adj[c][k] in 5-bit fields, k = 0..7
+    uint32_t bits24[8];    // [class of p]: bit[c][k] in 3-bit fields, k = 0..7
+    uint32_t dadj24[8];    // [class of p]: floor(r_c r_{k+1} / 30) - floor(r_c r_k / 30), 3-bit fields
 };
+
+// Gaps between consecutive residues coprime to 30 (1, 7, 11, ..., 29, 31) in
+// 4-bit fields: 6, 4, 2, 4, 2, 4, 6, 2.
+constexpr uint32_t kWheelGaps = 0x26424246u;
+// The residues 1, 7, 11, 13, 17, 19, 23, 29 in 5-bit fields.
+constexpr uint64_t kRes40 = 1ull | 7ull << 5 | 11ull << 10 | 13ull << 15 | 17ull << 20 | 19ull << 25 | 23ull << 30 |
+                            29ull << 35;
+// #{k : r_k <= x} for x = 0..29 in 4-bit fields (x < 16 in the low word, x >= 16 in the high word).
+constexpr uint64_t kCntLo = 0x4443322221111110ull;
+constexpr uint64_t kCntHi = 0x0087777776666554ull;
 
 __device__ __forceinline__ int wheel_index(uint32_t r) {
     int k = -1;
@@ -59,6 +72,21 @@ __device__ void init_tables(WheelTables &t) {
         int k = wheel_index(threadIdx.x);
         t.cls[threadIdx.x] = (uint8_t)(k < 0 ? 0xff : k);
     }
+    if (threadIdx.x < 8) {
+        const uint32_t rc = c_res[threadIdx.x];
+        uint32_t bits = 0, dadj = 0;
+        uint64_t adj = 0;
+        for (int k = 0; k < 8; ++k) {
+            adj |= (uint64_t)((rc * c_res[k]) / 30) << (5 * k);
+            const uint32_t rk = c_res[k], rk1 = k < 7 ? c_res[k + 1] : 31u;
+            bits |= (uint32_t)wheel_index((rc * rk) % 30) << (3 * k);
+            dadj |= ((rc * rk1) / 30 - (rc * rk) / 30) << (3 * k);
+        }
+        t.adj40[threadIdx.x] = adj;
+        t.bits24[threadIdx.x] = bits;
+        t.dadj24[threadIdx.x] = dadj;
+    }
+    __syncthreads();
 }
 
 // x mod p by Barrett reduction with M = floor((2^64 - 1) / p): the quotient
@@ -83,7 +111,7 @@ __device__ __forceinline__ void clear_bit(uint32_t *seg32, uint32_t off, uint32_
 __device__ __forceinline__ uint32_t class_off(const WheelTables &t, uint32_t p, uint32_t pq, uint32_t pc, int j,
                                               uint32_t R, int64_t B0, bool early, uint32_t L) {
     const uint32_t rj = c_res[j];
-    const uint32_t cj = pq * rj + t.adj[pc * 8 + j];
+    const uint32_t cj = pq * rj + (uint32_t)((t.adj40[pc] >> (5 * j)) & 31u);
     uint32_t d = cj - R;
     if ((int32_t)d < 0) d += p;
     if (!early) return d;
@@ -140,6 +168,123 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
+// Number of base primes among primes[0, n) with p^2 < E (a prefix, since the
+// primes ascend), found by one warp with 32-way probing.  Every lane of the
+// warp must call it; all lanes return the result.
+__device__ uint32_t primes_with_square_below(const uint32_t *primes, uint32_t n, uint64_t E, int lane) {
+    uint32_t a = 0, b = n;  // the answer lies in [a, b]
+    while (b - a > 32) {
+        const uint32_t step = (b - a + 31) / 32, idx = a + (uint32_t)lane * step;
+        bool ok = false;
+        if (idx < b) {
+            const uint64_t q = __ldg(primes + idx);
+            ok = q * q < E;
+        }
+        const int c = __popc(__ballot_sync(0xffffffffu, ok));
+        if (c == 0) return a;
+        const uint32_t na = a + (uint32_t)(c - 1) * step + 1, nb = a + (uint32_t)c * step;
+        a = na;
+        b = nb < b ? nb : b;
+    }
+    bool ok = false;
+    if (a + lane < b) {
+        const uint64_t q = __ldg(primes + a + lane);
+        ok = q * q < E;
+    }
+    return a + __popc(__ballot_sync(0xffffffffu, ok));
+}
+
+// Wheel cursor of a prime p: its multiples p m with m coprime to 30 in
+// increasing order.  In wheel bytes they are p a + c_k for a = 0, 1, ... and
+// k = 0..7, with c_k = floor(p r_k / 30) ascending in k, so stepping k -> k + 1
+// (and a -> a + 1 after k = 7) walks them in order.  wheel_start() returns the
+// first one at or after wheel byte B0 that also has m >= p (crossing starts at
+// p^2), as a byte offset from B0 (int64) and its class k.
+struct WheelCursor {
+    int64_t off;
+    uint32_t k;
+};
+
+__device__ __forceinline__ WheelCursor wheel_start_any(const WheelTables &t, uint32_t p, uint64_t M, uint32_t pq,
+                                                       uint32_t pc, int64_t B0) {
+    const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
+    uint64_t Q = __umul64hi(Bc, M);
+    uint32_t R = (uint32_t)(Bc - Q * p);
+    if (R >= p) {
+        R -= p;
+        ++Q;
+    }
+    uint32_t k = 0;  // first class with c_k >= R
+#pragma unroll
+    for (int j = 0; j < 8; ++j) k += (pq * c_res[j] + t.adj[pc * 8 + j]) < R;
+    uint64_t a = Q;
+    if (k == 8) {
+        k = 0;
+        ++a;
+    }
+    if (a < pq || (a == pq && k < pc)) {  // not before m = p: (a, k) >= (pq, class of p)
+        a = pq;
+        k = pc;
+    }
+    uint32_t c_k = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if ((uint32_t)j == k) c_k = pq * c_res[j] + t.adj[pc * 8 + j];
+    WheelCursor w;
+    w.off = (int64_t)((uint64_t)p * a + c_k) - B0;
+    w.k = k;
+    return w;
+}
+
+// wheel_start for a segment that cannot begin before p^2 (see is_early): the
+// first multiple at or after B0 is p Q + c_k with R = B0 mod p and k the first
+// class with c_k >= R.  Since c_k = floor(p r_k / 30), c_k >= R exactly when
+// p r_k >= 30 R, so k = #{r_k < 30 R / p}: estimated in single precision, then
+// corrected with the exact integer test (the estimate is off by at most one
+// class).  Offsets are then 32-bit: c_k - R, or p + c_0 - R past class 7.
+__device__ __forceinline__ WheelCursor wheel_start_late(uint64_t adj, uint32_t p, uint64_t M, uint32_t pq,
+                                                        uint64_t Bc) {
+    const uint32_t R = mod_barrett(Bc, p, M);
+    const uint64_t x30 = 30ull * R;
+    float tf = (float)x30 * __frcp_rn((float)p);
+    uint32_t x = tf < 29.0f ? (uint32_t)tf : 29u;
+    uint32_t k = (uint32_t)((x < 16 ? kCntLo >> (4 * x) : kCntHi >> (4 * (x - 16))) & 15u);
+    if (k < 8 && (uint64_t)p * ((kRes40 >> (5 * k)) & 31u) < x30)
+        ++k;
+    else if (k > 0 && (uint64_t)p * ((kRes40 >> (5 * (k - 1))) & 31u) >= x30)
+        --k;
+    WheelCursor w;
+    if (k == 8) {
+        w.off = (int64_t)(p + pq - R);  // class 0 of the next block: p + c_0 - R, c_0 = pq
+        w.k = 0;
+    } else {
+        w.off = (int64_t)(pq * (uint32_t)((kRes40 >> (5 * k)) & 31u) + (uint32_t)((adj >> (5 * k)) & 31u) - R);
+        w.k = k;
+    }
+    return w;
+}
+
+__device__ __forceinline__ WheelCursor wheel_start(const WheelTables &t, uint32_t p, uint64_t M, uint32_t pq,
+                                                   uint32_t pc, int64_t B0) {
+    const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
+    if (is_early(B0, Bc, p)) return wheel_start_any(t, p, M, pq, pc, B0);
+    return wheel_start_late(t.adj40[pc], p, M, pq, Bc);
+}
+
+// Byte distance from multiple (a, k) to the next one: pq gap_k + dadj_k.
+__device__ __forceinline__ uint32_t wheel_step(uint32_t pq, uint32_t dadj, uint32_t k) {
+    return pq * ((kWheelGaps >> (4 * k)) & 15u) + ((dadj >> (3 * k)) & 7u);
+}
+
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(1024, 1) k_sieve(SieveLaunch P) {
     extern __shared__ uint4 smem4[];
@@ -150,12 +295,15 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(SieveLaunch P) {
     __shared__ uint32_t s_range;
     __shared__ uint32_t s_small_next;
     __shared__ unsigned long long s_red[32];
-    __shared__ uint32_t s_R[kSmallResidues];  // B0 mod p for the first small primes
-    __shared__ uint32_t s_nseg;                 // base primes with p^2 below the segment end
+    __shared__ uint32_t s_R[kSmallResidues];      // B0 mod p for the first small primes
+    __shared__ uint32_t s_nseg;                     // base primes with p^2 below the segment end
+    __shared__ uint32_t s_nbucket;                  // bucket primes with p^2 below the chunk end
+    __shared__ uint32_t s_cnt[kMaxChunkSegments];  // bucket fill counts, one per segment of the chunk
 
     init_tables(tab);
     const int tid = threadIdx.x, lane = tid & 31;
-    const uint32_t S = P.seg_bytes;
+    const uint32_t S = P.seg_bytes, C = P.chunk_segs;
+    uint32_t *const bucket_base = P.buckets ? P.buckets + (size_t)blockIdx.x * C * P.bucket_cap : nullptr;
 
     for (;;) {
         if (tid == 0) {
@@ -169,236 +317,283 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(SieveLaunch P) {
                 }
                 s_range = a;
             }
-            s_small_next = 0;
         }
+        if (tid < (int)C) s_cnt[tid] = 0;
         __syncthreads();
         const unsigned long long item = s_item;
         if (item >= P.n_items) break;
         const RangeDesc &rd = P.ranges[s_range];
-        const uint64_t s = item - rd.item_first;
-        const int64_t B0 = rd.Bbase + (int64_t)(s * S);
-        const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
-        const int64_t base_int = 30 * B0;  // integer of bit 0 of byte 0
-        const int64_t hi_rel = (int64_t)rd.hi - base_int, lo_rel = (int64_t)rd.lo - base_int;
-        uint32_t L;
-        {
-            int64_t need = (hi_rel + 29) / 30;
-            need = (need + 31) & ~(int64_t)31;
-            L = need < (int64_t)S ? (uint32_t)need : S;
-        }
+        const uint32_t range_id = s_range;
+        // this item: segments [s0, s0 + nchunk) of the range
+        const uint64_t s0 = (item - rd.item_first) * C;
+        const uint32_t nchunk = (uint32_t)(rd.nseg - s0 < C ? rd.nseg - s0 : C);
+        const int64_t Bs = rd.Bbase + (int64_t)(s0 * S);
         const uint32_t n_range = rd.n_use;
-
-        // 1. pre-sieved pattern -> shared memory (16-byte aligned copy)
+        uint32_t chunk_bytes;
         {
-            int64_t ph = B0 % (int64_t)kTilePeriod;
-            if (ph < 0) ph += kTilePeriod;
-            const uint32_t k = (uint32_t)ph & 15u;
-            const uint4 *src = reinterpret_cast<const uint4 *>(P.tile + k * P.tile_stride + ((uint32_t)ph - k));
-            for (uint32_t i = tid; i < L / 16; i += blockDim.x) smem4[i] = __ldg(src + i);
+            int64_t need = ((int64_t)rd.hi - 30 * Bs + 29) / 30;
+            need = (need + 31) & ~(int64_t)31;
+            const int64_t full = (int64_t)nchunk * S;
+            chunk_bytes = (uint32_t)(need < full ? need : full);
         }
-        // primes with p^2 >= the segment's end have no multiple to cross here:
-        // warp 0 finds how many base primes remain (32-way search)
-        if (tid < 32) {
-            const int64_t seg_end = base_int + 30 * (int64_t)L;
-            const uint64_t E = (uint64_t)(seg_end < (int64_t)rd.hi ? seg_end : (int64_t)rd.hi);
-            uint32_t a = 0, b = n_range;
-            while (b - a > 32) {
-                const uint32_t step = (b - a + 31) / 32, idx = a + (uint32_t)lane * step;
-                bool ok = false;
-                if (idx < b) {
-                    const uint64_t q = __ldg(P.primes + idx);
-                    ok = q * q < E;
-                }
-                const int c = __popc(__ballot_sync(0xffffffffu, ok));
-                if (c == 0) {
-                    b = a;
-                    break;
-                }
-                const uint32_t na = a + (uint32_t)(c - 1) * step + 1, nb = a + (uint32_t)c * step;
-                a = na;
-                b = nb < b ? nb : b;
-            }
-            bool ok = false;
-            if (a + lane < b) {
-                const uint64_t q = __ldg(P.primes + a + lane);
-                ok = q * q < E;
-            }
-            const uint32_t n = a + __popc(__ballot_sync(0xffffffffu, ok));
-            if (lane == 0) s_nseg = n;
-        }
-        {
-            const uint32_t se = P.small_end < n_range ? P.small_end : n_range;
-            const uint32_t nr = se > kFirstCrossingPrime ? se - kFirstCrossingPrime : 0;
-            for (uint32_t t = tid; t < nr && t < kSmallResidues; t += blockDim.x)
-                s_R[t] = mod_barrett(Bc, __ldg(P.primes + kFirstCrossingPrime + t),
-                                     __ldg(P.magic + kFirstCrossingPrime + t));
-        }
-        __syncthreads();
-        const uint32_t n_use = s_nseg;
-        const uint32_t small_end = P.small_end < n_use ? P.small_end : n_use;
-        const uint32_t n_small8 = (small_end > kFirstCrossingPrime ? small_end - kFirstCrossingPrime : 0) * 8;
 
-        // 2a. medium primes [small_end, mid_end): one lane per prime, the warp
-        //     taking 32 consecutive primes at a time (warp-uniform loop, so
-        //     the lanes can be re-converged after every sub-loop).  Each of the
-        //     eight progressions (stride p bytes) is split into four
-        //     sub-progressions of stride 4 p bytes = p words, one per byte
-        //     phase, each crossed with one fixed mask.
-        const uint32_t mid_end = P.mid_end < n_use ? P.mid_end : n_use;
-        const uint32_t Lw = L >> 2;
-        for (uint32_t base = P.small_end + (tid & ~31u); base < mid_end; base += blockDim.x) {
-            const uint32_t i = base + lane;
-            const bool valid = i < mid_end;
-            const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
-            const uint64_t M = valid ? __ldg(P.magic + i) : ~0ull;
-            const uint32_t R = mod_barrett(Bc, p, M);
-            const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
-            const bool early = valid && is_early(B0, Bc, p);
-            if (early) cross_prime_early(tab, seg32, p, pq, pc, R, B0, L);
-            __syncwarp();
-            const uint32_t lw = (valid && !early) ? Lw : 0u;  // fast path only for the others
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, false, L);
-                const uint32_t bit = tab.bit[pc * 8 + j];
-#pragma unroll
-                for (uint32_t ph = 0; ph < 4; ++ph) {
-                    // p^-1 = p (mod 4), so off + k p = ph (mod 4) for k = (ph - off) p mod 4
-                    const uint32_t o = off + (((ph - off) * p) & 3u) * p;
-                    const uint32_t mask = ~(1u << (8u * ph + bit));
-                    for (uint32_t w = o >> 2; w < lw; w += p) atomicAnd(&seg32[w], mask);
+        // 0. bucket fill: every bucket prime with a multiple in this chunk
+        //    appends its hits to the chunk's per-segment lists (in HBM)
+        const bool use_buckets = P.bucket_first < n_range;
+        if (use_buckets) {
+            if (tid < 32) {
+                const uint64_t E = (uint64_t)(30 * (Bs + (int64_t)chunk_bytes));
+                const uint64_t Eh = E < rd.hi ? E : rd.hi;
+                const uint32_t n = primes_with_square_below(P.primes, n_range, Eh, lane);
+                if (lane == 0) s_nbucket = n;
+            }
+            __syncthreads();
+            // one lane per bucket prime, 32 primes per warp: for each segment of
+            // the chunk the warp counts its lanes' hits, reserves room with one
+            // shared-memory atomic, and each lane writes its hits contiguously
+            const uint32_t nb = s_nbucket;
+            for (uint32_t base = P.bucket_first + (tid & ~31u); base < nb; base += blockDim.x) {
+                const uint32_t i = base + lane;
+                const bool valid = i < nb;
+                const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
+                const uint64_t M = valid ? __ldg(P.magic + i) : ~0ull;
+                const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
+                WheelCursor wc = wheel_start(tab, p, M, pq, pc, Bs);
+                uint32_t off = (valid && wc.off < (int64_t)chunk_bytes) ? (uint32_t)wc.off : chunk_bytes;
+                uint32_t k = wc.k;
+                const uint32_t bits = tab.bits24[pc], dadj = tab.dadj24[pc];
+                for (uint32_t g = 0; g < nchunk; ++g) {
+                    const uint32_t seg_lo = g * S, seg_end = seg_lo + S < chunk_bytes ? seg_lo + S : chunk_bytes;
+                    uint32_t h = 0;
+                    for (uint32_t o = off, kk = k; o < seg_end; o += wheel_step(pq, dadj, kk), kk = (kk + 1) & 7u) ++h;
+                    __syncwarp();
+                    const uint32_t incl = warp_inclusive_scan(h, lane);
+                    uint32_t first = 0;
+                    if (lane == 31 && incl) first = atomicAdd(s_cnt + g, incl);
+                    first = __shfl_sync(0xffffffffu, first, 31) + incl - h;
+                    uint32_t *list = bucket_base + (size_t)g * P.bucket_cap;
+                    for (; off < seg_end; off += wheel_step(pq, dadj, k), k = (k + 1) & 7u, ++first) {
+                        const uint32_t wo = off - seg_lo;
+                        const uint32_t bit = (bits >> (3 * k)) & 7u;
+                        if (first < P.bucket_cap)
+                            list[first] = (wo >> 2) | ((((wo & 3u) << 3) | bit) << 16);
+                        else
+                            atomicOr(P.overflow, 1u);
+                    }
+                    __syncwarp();
                 }
+            }
+            __syncthreads();
+        }
+
+        for (uint32_t g = 0; g < nchunk; ++g) {
+            const uint64_t s = s0 + g;
+            const int64_t B0 = Bs + (int64_t)g * S;
+            const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
+            const int64_t base_int = 30 * B0;  // integer of bit 0 of byte 0
+            const int64_t hi_rel = (int64_t)rd.hi - base_int, lo_rel = (int64_t)rd.lo - base_int;
+            const uint32_t L = chunk_bytes - g * S < S ? chunk_bytes - g * S : S;
+
+            // 1. pre-sieved pattern -> shared memory (16-byte aligned copy)
+            {
+                int64_t ph = B0 % (int64_t)kTilePeriod;
+                if (ph < 0) ph += kTilePeriod;
+                const uint32_t k = (uint32_t)ph & 15u;
+                const uint4 *src = reinterpret_cast<const uint4 *>(P.tile + k * P.tile_stride + ((uint32_t)ph - k));
+                for (uint32_t i = tid; i < L / 16; i += blockDim.x) smem4[i] = __ldg(src + i);
+            }
+            // primes with p^2 >= the segment's end have no multiple to cross here
+            if (tid < 32) {
+                const int64_t seg_end = base_int + 30 * (int64_t)L;
+                const uint64_t E = (uint64_t)(seg_end < (int64_t)rd.hi ? seg_end : (int64_t)rd.hi);
+                const uint32_t n = primes_with_square_below(P.primes, n_range, E, lane);
+                if (lane == 0) {
+                    s_nseg = n;
+                    s_small_next = 0;
+                }
+            }
+            {
+                const uint32_t se = P.small_end < n_range ? P.small_end : n_range;
+                const uint32_t nr = se > kFirstCrossingPrime ? se - kFirstCrossingPrime : 0;
+                for (uint32_t t = tid; t < nr && t < kSmallResidues; t += blockDim.x)
+                    s_R[t] = mod_barrett(Bc, __ldg(P.primes + kFirstCrossingPrime + t),
+                                         __ldg(P.magic + kFirstCrossingPrime + t));
+            }
+            __syncthreads();
+            const uint32_t n_seg = s_nseg;
+            // primes crossed here (not through the buckets): [8, n_use)
+            const uint32_t n_use = use_buckets && P.bucket_first < n_seg ? P.bucket_first : n_seg;
+            const uint32_t small_end = P.small_end < n_use ? P.small_end : n_use;
+            const uint32_t n_small8 = (small_end > kFirstCrossingPrime ? small_end - kFirstCrossingPrime : 0) * 8;
+
+            // 2a. medium primes [small_end, mid_end): one lane per prime, the warp
+            //     taking 32 consecutive primes at a time (warp-uniform loop, so
+            //     the lanes can be re-converged after every sub-loop).  Each of
+            //     the eight progressions (stride p bytes) is split into four
+            //     sub-progressions of stride 4 p bytes = p words, one per byte
+            //     phase, each crossed with one fixed mask.
+            const uint32_t mid_end = P.mid_end < n_use ? P.mid_end : n_use;
+            const uint32_t Lw = L >> 2;
+            for (uint32_t base = P.small_end + (tid & ~31u); base < mid_end; base += blockDim.x) {
+                const uint32_t i = base + lane;
+                const bool valid = i < mid_end;
+                const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
+                const uint64_t M = valid ? __ldg(P.magic + i) : ~0ull;
+                const uint32_t R = mod_barrett(Bc, p, M);
+                const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
+                const bool early = valid && is_early(B0, Bc, p);
+                if (early) cross_prime_early(tab, seg32, p, pq, pc, R, B0, L);
+                __syncwarp();
+                const uint32_t lw = (valid && !early) ? Lw : 0u;  // fast path only for the others
+                const uint32_t bits = tab.bits24[pc];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, false, L);
+                    const uint32_t bit = (bits >> (3 * j)) & 7u;
+#pragma unroll
+                    for (uint32_t ph = 0; ph < 4; ++ph) {
+                        // p^-1 = p (mod 4), so off + k p = ph (mod 4) for k = (ph - off) p mod 4
+                        const uint32_t o = off + (((ph - off) * p) & 3u) * p;
+                        const uint32_t mask = ~(1u << (8u * ph + bit));
+                        for (uint32_t w = o >> 2; w < lw; w += p) atomicAnd(&seg32[w], mask);
+                    }
+                    __syncwarp();
+                }
+            }
+            // 2a'. large primes below the bucket limit [mid_end, n_use): one lane
+            //      per prime, walking its multiples in the segment with the wheel
+            //      cursor (only the hits are visited, not all eight classes)
+            for (uint32_t base = mid_end + (tid & ~31u); base < n_use; base += blockDim.x) {
+                const uint32_t i = base + lane;
+                const bool valid = i < n_use;
+                const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
+                const uint64_t M = valid ? __ldg(P.magic + i) : ~0ull;
+                const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
+                const WheelCursor wc = wheel_start(tab, p, M, pq, pc, B0);
+                uint32_t off = (valid && wc.off < (int64_t)L) ? (uint32_t)wc.off : L;
+                uint32_t k = wc.k;
+                const uint32_t bits = tab.bits24[pc], dadj = tab.dadj24[pc];
+                for (; off < L; off += wheel_step(pq, dadj, k), k = (k + 1) & 7u)
+                    clear_bit(seg32, off, (bits >> (3 * k)) & 7u);
                 __syncwarp();
             }
-        }
-        // 2a'. large primes [mid_end, n_use): one lane per prime, at most a
-        //      few hits per progression, crossed directly
-        for (uint32_t base = mid_end + (tid & ~31u); base < n_use; base += blockDim.x) {
-            const uint32_t i = base + lane;
-            const bool valid = i < n_use;
-            const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
-            const uint64_t M = valid ? __ldg(P.magic + i) : ~0ull;
-            const uint32_t R = mod_barrett(Bc, p, M);
-            const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
-            const bool early = valid && is_early(B0, Bc, p);
-            if (early) cross_prime_early(tab, seg32, p, pq, pc, R, B0, L);
-            __syncwarp();
-            const uint32_t l = (valid && !early) ? L : 0u;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, false, L);
+            // 2c. drain this segment's bucket list
+            if (use_buckets) {
+                const uint32_t n = s_cnt[g] < P.bucket_cap ? s_cnt[g] : P.bucket_cap;
+                const uint32_t *list = bucket_base + (size_t)g * P.bucket_cap;
+                for (uint32_t e = tid; e < n; e += blockDim.x) {
+                    const uint32_t v = list[e];
+                    atomicAnd(&seg32[v & 0xffffu], ~(1u << (v >> 16)));
+                }
+            }
+            // 2b. small primes [8, small_end): one (prime, class) progression per
+            //     warp, taken dynamically in decreasing order of work.  The
+            //     progression (stride p bytes) is split into 128 sub-progressions
+            //     of stride 128 p: lane l takes the four whose bytes are 4 l + q
+            //     (mod 128), q = 0..3.  Every lane then always writes bank l of
+            //     the segment with one fixed bit mask, so a warp's 32 atomics
+            //     never share a bank and need no per-hit mask arithmetic.
+            for (;;) {
+                uint32_t k = 0;
+                if (lane == 0) k = atomicAdd(&s_small_next, 1u);
+                k = __shfl_sync(0xffffffffu, k, 0);
+                if (k >= n_small8) break;
+                const uint32_t i = kFirstCrossingPrime + (k >> 3);
+                const int j = (int)(k & 7);
+                const uint32_t p = __ldg(P.primes + i);
+                const uint32_t t = i - kFirstCrossingPrime;
+                const uint32_t R = t < kSmallResidues ? s_R[t] : mod_barrett(Bc, p, __ldg(P.magic + i));
+                const uint32_t pq = p / 30, pc = tab.cls[p - pq * 30];
+                const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, is_early(B0, Bc, p), L);
+                if (off >= L) continue;
                 const uint32_t bit = tab.bit[pc * 8 + j];
-                for (uint32_t o = off; o < l; o += p) clear_bit(seg32, o, bit);
-            }
-            __syncwarp();
-        }
-        // 2b. small primes [8, small_end): one (prime, class) progression per
-        //     warp, taken dynamically in decreasing order of work.  The
-        //     progression (stride p bytes) is split into 128 sub-progressions of
-        //     stride 128 p: lane l takes the four whose bytes are 4 l + q
-        //     (mod 128), q = 0..3.  Every lane then always writes bank l of the
-        //     segment with one fixed bit mask, so a warp's 32 atomics never share
-        //     a bank and need no per-hit mask arithmetic.
-        for (;;) {
-            uint32_t k = 0;
-            if (lane == 0) k = atomicAdd(&s_small_next, 1u);
-            k = __shfl_sync(0xffffffffu, k, 0);
-            if (k >= n_small8) break;
-            const uint32_t i = kFirstCrossingPrime + (k >> 3);
-            const int j = (int)(k & 7);
-            const uint32_t p = __ldg(P.primes + i);
-            const uint32_t t = i - kFirstCrossingPrime;
-            const uint32_t R = t < kSmallResidues ? s_R[t] : mod_barrett(Bc, p, __ldg(P.magic + i));
-            const uint32_t pq = p / 30, pc = tab.cls[p - pq * 30];
-            const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, is_early(B0, Bc, p), L);
-            if (off >= L) continue;
-            const uint32_t bit = tab.bit[pc * 8 + j];
-            const uint32_t pinv = inv_mod128(p);
-            const uint32_t Lw = L >> 2, wstep = 32u * p;  // 128 p bytes = 32 p words
+                const uint32_t pinv = inv_mod128(p);
+                const uint32_t wstep = 32u * p;  // 128 p bytes = 32 p words
 #pragma unroll
-            for (uint32_t q = 0; q < 4; ++q) {
-                const uint32_t kappa = ((4u * (uint32_t)lane + q - off) * pinv) & 127u;
-                const uint32_t o = off + kappa * p;  // = 4 lane + q (mod 128)
-                const uint32_t mask = ~(1u << (8u * q + bit));
+                for (uint32_t q = 0; q < 4; ++q) {
+                    const uint32_t kappa = ((4u * (uint32_t)lane + q - off) * pinv) & 127u;
+                    const uint32_t o = off + kappa * p;  // = 4 lane + q (mod 128)
+                    const uint32_t mask = ~(1u << (8u * q + bit));
 #pragma unroll 4
-                for (uint32_t w = o >> 2; w < Lw; w += wstep) atomicAnd(&seg32[w], mask);
-            }
-        }
-        __syncthreads();
-
-        // 3. the byte holding integers 0..29: 1 is not prime, 7..19 are
-        if (tid == 0 && B0 <= 0 && B0 + (int64_t)L > 0) seg[-B0] = 0xFE;
-        __syncthreads();
-
-        unsigned long long cnt = 0;
-        if (MODE == kModeCount) {
-            // 4. popcount of the bits in [lo, hi)
-            for (uint32_t w = tid; w < L / 4; w += blockDim.x) {
-                uint32_t v = seg32[w];
-                const int64_t wb = 120 * (int64_t)w;
-                if (wb < lo_rel || wb + 120 > hi_rel) v &= range_mask(wb, lo_rel, hi_rel);
-                cnt += __popc(v);
-            }
-        } else {
-            // 4'. expand each group of 32 wheel bytes (960 integers) into 15
-            //     words of the odd-only bitmap and store them
-            const uint64_t nwords = rd.bitmap_words;
-            const uint64_t o0 = rd.lo | 1;
-            const uint64_t nbits = o0 < rd.hi ? (rd.hi - o0 + 1) / 2 : 0;
-            uint32_t *out = rd.bitmap;
-            for (uint32_t g = tid; g < L / 32; g += blockDim.x) {
-                const int64_t n0 = base_int + 960 * (int64_t)g + 1;  // first odd integer of the group
-                const int64_t w0 = (n0 - (int64_t)o0) / 64;         // exact: n0 = o0 (mod 64)
-                if (w0 + 15 <= 0 || w0 >= (int64_t)nwords) continue;
-                uint32_t wv[8];
-                const uint4 a = smem4[2 * g], b = smem4[2 * g + 1];
-                wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
-                wv[4] = b.x; wv[5] = b.y; wv[6] = b.z; wv[7] = b.w;
-                uint32_t o[15];
-#pragma unroll
-                for (int q = 0; q < 15; ++q) o[q] = 0;
-#pragma unroll
-                for (int bb = 0; bb < 32; ++bb) {
-                    const uint32_t e = tab.expand[(wv[bb >> 2] >> (8 * (bb & 3))) & 0xffu];
-                    const int pos = 15 * bb, wi = pos >> 5, sh = pos & 31;
-                    o[wi] |= e << sh;
-                    if (sh > 17) o[wi + 1] |= e >> (32 - sh);
+                    for (uint32_t w = o >> 2; w < Lw; w += wstep) atomicAnd(&seg32[w], mask);
                 }
-                // 3 and 5 are prime but have no wheel bit
-                if (n0 <= 5 && n0 + 958 >= 3) {
-#pragma unroll
-                    for (int sp = 3; sp <= 5; sp += 2) {
-                        const int64_t k = (sp - n0) / 2;
-                        if (sp >= n0 && k < 480) {
-#pragma unroll
-                            for (int q = 0; q < 15; ++q)  // compile-time register index
-                                if ((k >> 5) == q) o[q] |= 1u << (k & 31);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 15; ++q) {
-                    const int64_t wq = w0 + q;
-                    if (wq < 0 || wq >= (int64_t)nwords) continue;
-                    uint32_t v = o[q];
-                    if (wq == (int64_t)nwords - 1 && (nbits & 31)) v &= (1u << (nbits & 31)) - 1u;
-                    if (out) out[wq] = v;
+            }
+            __syncthreads();
+
+            // 3. the byte holding integers 0..29: 1 is not prime, 7..19 are
+            if (tid == 0 && B0 <= 0 && B0 + (int64_t)L > 0) seg[-B0] = 0xFE;
+            __syncthreads();
+
+            unsigned long long cnt = 0;
+            if (MODE == kModeCount) {
+                // 4. popcount of the bits in [lo, hi)
+                for (uint32_t w = tid; w < L / 4; w += blockDim.x) {
+                    uint32_t v = seg32[w];
+                    const int64_t wb = 120 * (int64_t)w;
+                    if (wb < lo_rel || wb + 120 > hi_rel) v &= range_mask(wb, lo_rel, hi_rel);
                     cnt += __popc(v);
                 }
+            } else {
+                // 4'. expand each group of 32 wheel bytes (960 integers) into 15
+                //     words of the odd-only bitmap and store them
+                const uint64_t nwords = rd.bitmap_words;
+                const uint64_t o0 = rd.lo | 1;
+                const uint64_t nbits = o0 < rd.hi ? (rd.hi - o0 + 1) / 2 : 0;
+                uint32_t *out = rd.bitmap;
+                for (uint32_t gr = tid; gr < L / 32; gr += blockDim.x) {
+                    const int64_t n0 = base_int + 960 * (int64_t)gr + 1;  // first odd integer of the group
+                    const int64_t w0 = (n0 - (int64_t)o0) / 64;          // exact: n0 = o0 (mod 64)
+                    if (w0 + 15 <= 0 || w0 >= (int64_t)nwords) continue;
+                    uint32_t wv[8];
+                    const uint4 a = smem4[2 * gr], b = smem4[2 * gr + 1];
+                    wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
+                    wv[4] = b.x; wv[5] = b.y; wv[6] = b.z; wv[7] = b.w;
+                    uint32_t o[15];
+#pragma unroll
+                    for (int q = 0; q < 15; ++q) o[q] = 0;
+#pragma unroll
+                    for (int bb = 0; bb < 32; ++bb) {
+                        const uint32_t e = tab.expand[(wv[bb >> 2] >> (8 * (bb & 3))) & 0xffu];
+                        const int pos = 15 * bb, wi = pos >> 5, sh = pos & 31;
+                        o[wi] |= e << sh;
+                        if (sh > 17) o[wi + 1] |= e >> (32 - sh);
+                    }
+                    // 3 and 5 are prime but have no wheel bit
+                    if (n0 <= 5 && n0 + 958 >= 3) {
+#pragma unroll
+                        for (int sp = 3; sp <= 5; sp += 2) {
+                            const int64_t k = (sp - n0) / 2;
+                            if (sp >= n0 && k < 480) {
+#pragma unroll
+                                for (int q = 0; q < 15; ++q)  // compile-time register index
+                                    if ((k >> 5) == q) o[q] |= 1u << (k & 31);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 15; ++q) {
+                        const int64_t wq = w0 + q;
+                        if (wq < 0 || wq >= (int64_t)nwords) continue;
+                        uint32_t v = o[q];
+                        if (wq == (int64_t)nwords - 1 && (nbits & 31)) v &= (1u << (nbits & 31)) - 1u;
+                        if (out) out[wq] = v;
+                        cnt += __popc(v);
+                    }
+                }
             }
-        }
-        cnt = warp_sum(cnt);
-        if (lane == 0) s_red[tid >> 5] = cnt;
-        __syncthreads();
-        if (tid < 32) {
-            unsigned long long v = tid < (int)(blockDim.x >> 5) ? s_red[tid] : 0ull;
-            v = warp_sum(v);
-            if (tid == 0) {
-                if (s == 0) v += rd.corr;
-                atomicAdd(P.counts + s_range, v);
+            cnt = warp_sum(cnt);
+            if (lane == 0) s_red[tid >> 5] = cnt;
+            __syncthreads();
+            if (tid < 32) {
+                unsigned long long v = tid < (int)(blockDim.x >> 5) ? s_red[tid] : 0ull;
+                v = warp_sum(v);
+                if (tid == 0) {
+                    if (s == 0) v += rd.corr;
+                    atomicAdd(P.counts + range_id, v);
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -541,6 +736,10 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t *bitmap, uint64_t n
 template <typename T>
 __global__ void k_put_two(T *out) { out[0] = (T)2; }
 
+__global__ void k_finalize_count(const unsigned long long *count, const unsigned *overflow, uint64_t *out) {
+    *out = *overflow ? ~0ull : *count;
+}
+
 }  // namespace
 
 cudaError_t set_sieve_smem_limits() {
@@ -602,6 +801,12 @@ cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t 
     else
         k_emit<uint32_t><<<g, 256, 0, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
                                                 static_cast<uint32_t *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_count(const unsigned long long *count, const unsigned *overflow, uint64_t *out,
+                                  cudaStream_t stream) {
+    k_finalize_count<<<1, 1, 0, stream>>>(count, overflow, out);
     return cudaGetLastError();
 }
 

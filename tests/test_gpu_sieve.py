@@ -125,16 +125,23 @@ def test_multi_segment_ranges_several_grid_phases(sv):
         assert np.array_equal(words, oracle.bitmap(lo, hi)), (lo, hi)
 
 
-@pytest.mark.parametrize("seg,threads,small,ctas", [(1024, 256, 23, 1), (4096 + 32, 512, 100, 2),
-                                                     (65536, 1024, 65536, 1), (229376, 1024, 7168, 1),
-                                                     (32 * 1001, 256, 2000, 3)])
-def test_launch_parameters_do_not_change_results(seg, threads, small, ctas):
+@pytest.mark.parametrize("seg,threads,small,ctas,chunk,blim", [
+    (1024, 256, 23, 1, 1, 0), (4096 + 32, 512, 100, 2, 7, 0), (65536, 1024, 65536, 1, 64, 0),
+    (229376, 1024, 7168, 1, 16, 0), (32 * 1001, 256, 2000, 3, 3, 0),
+    # most primes through the bucket lists, several hits per list per prime
+    (229376, 1024, 1792, 1, 16, 30), (8192, 512, 60, 1, 64, 100), (229376, 1024, 1792, 1, 1, 2000),
+    # no bucket lists at all
+    (229376, 1024, 1792, 1, 16, 1 << 40)])
+def test_launch_parameters_do_not_change_results(seg, threads, small, ctas, chunk, blim):
     with gb.Sieve(10**13) as s:
         s.set_param(gb.SIEVE_PARAM_SEGMENT_BYTES, seg)
         s.set_param(gb.SIEVE_PARAM_THREADS, threads)
         s.set_param(gb.SIEVE_PARAM_SMALL_LIMIT, small)
         s.set_param(gb.SIEVE_PARAM_CTAS_PER_SM, ctas)
-        for lo, hi in [(0, 10**7), (123_456_789_012, 123_456_789_012 + 3 * 10**6), (5, 40_000)]:
+        s.set_param(gb.SIEVE_PARAM_CHUNK_SEGMENTS, chunk)
+        s.set_param(gb.SIEVE_PARAM_BUCKET_LIMIT, blim)
+        for lo, hi in [(0, 10**7), (123_456_789_012, 123_456_789_012 + 3 * 10**6), (5, 40_000),
+                       (9 * 10**12, 9 * 10**12 + 2 * 10**7)]:
             assert s.count(lo, hi) == oracle.count(lo, hi)
             words, _ = s.bitmap(lo, hi)
             assert np.array_equal(words.cpu().numpy().view(np.uint32), oracle.bitmap(lo, hi))
