@@ -155,6 +155,83 @@ int sieve_compact_static(const uint32_t *bitmap_dev, uint64_t lo, uint64_t hi,
                          uint32_t *out_dev, size_t cap, uint64_t *n,
                          void *cuda_stream);
 
+/*
+ * ---------------------------------------------------------------- serving
+ * A request server on a context: sieve requests of mixed sizes arrive at any
+ * time from any host thread and are sieved by continuous batching.  A host
+ * scheduler thread splits every admitted request into runs of consecutive
+ * segments; each scheduling tick launches ONE persistent sieve kernel over
+ * runs taken from all requests that still have work (at most tick_segments
+ * segments in all), and up to two ticks are in flight on the GPU.  A request
+ * that arrives while others run joins the next tick, so short requests are
+ * not stuck behind long ones, and a long request advances a few segments per
+ * tick.  Base primes and the pattern tile are the context's, shared
+ * read-only; the server has its own streams and buffers, so the context stays
+ * usable from other threads.  A request's result does not depend on what else
+ * is in flight: every run is sieved the same way as by sieve_count, and the
+ * runs of a request partition its range.
+ *
+ * Admission: a request is rejected with SIEVE_EBUSY when max_requests are in
+ * flight or, for a list request, when its device memory -- the odd-only bitmap
+ * plus room for at most 2 w / ln w + 64 primes, w = hi - lo (the
+ * Montgomery-Vaughan form of the Brun-Titchmarsh bound on primes in an
+ * interval) -- does not fit in what is left of max_device_bytes.
+ */
+typedef struct sieve_server sieve_server;
+
+#define SIEVE_REQ_COUNT 0 /* result: the count */
+#define SIEVE_REQ_LIST  1 /* result: the count and the ascending primes (uint64, host) */
+
+typedef struct {
+    uint32_t max_requests;     /* requests admitted and not yet released (0: 1024) */
+    uint32_t tick_segments;    /* segments per scheduling tick (0: 4 x SMs) */
+    uint64_t max_device_bytes; /* device memory for list requests (0: 4 GiB) */
+} sieve_server_cfg;
+
+typedef struct {
+    uint64_t lo, hi; /* the range [lo, hi), hi <= the context's hi_max */
+    int32_t kind;    /* SIEVE_REQ_COUNT or SIEVE_REQ_LIST */
+    int32_t reserved;
+} sieve_req;
+
+typedef struct {
+    int32_t status;         /* SIEVE_OK, or the error this request failed with */
+    int32_t kind;
+    uint64_t count;         /* primes in [lo, hi) */
+    const uint64_t *primes; /* SIEVE_REQ_LIST: `count` primes, host memory owned by the
+                               server, valid until sieve_server_release; else NULL */
+    double latency_us;      /* from submit to the result being ready on the host */
+} sieve_result;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, ticks;
+    uint64_t integers;      /* sum of hi - lo over completed requests */
+    uint32_t in_flight;     /* admitted, not yet completed */
+    uint32_t reserved;
+    uint64_t device_bytes_reserved;
+} sieve_server_counters;
+
+/* Start a server on ctx (cfg may be NULL for defaults).  ctx must outlive it. */
+int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_server **out);
+
+/* Admit a request; *ticket identifies it.  SIEVE_EBUSY if it does not fit now,
+ * SIEVE_EINVAL / SIEVE_ERANGE for a bad range or kind.  Never blocks on GPU work. */
+int sieve_server_submit(sieve_server *srv, const sieve_req *req, uint64_t *ticket);
+
+/* Wait up to timeout_us microseconds (< 0: no limit) for a request's result.
+ * SIEVE_ETIMEOUT if it is not ready by then, SIEVE_ENOENT for an unknown or
+ * released ticket.  May be called again after a timeout or a success. */
+int sieve_server_poll(sieve_server *srv, uint64_t ticket, sieve_result *res, int64_t timeout_us);
+
+/* Forget a completed request and free its result (SIEVE_EBUSY if not done). */
+int sieve_server_release(sieve_server *srv, uint64_t ticket);
+
+/* Counters since creation. */
+int sieve_server_stats(sieve_server *srv, sieve_server_counters *st);
+
+/* Finish the work in flight, stop the scheduler and free the server. */
+void sieve_server_destroy(sieve_server *srv);
+
 /* Tunable launch parameters (see sieve_set_param / sieve_get_param). */
 #define SIEVE_PARAM_SEGMENT_BYTES 1 /* shared-memory segment, bytes; multiple of 32 */
 #define SIEVE_PARAM_THREADS       2 /* threads per CTA: 256, 512 or 1024 */

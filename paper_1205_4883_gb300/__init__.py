@@ -47,6 +47,29 @@ class sieve_info(ctypes.Structure):
                 ("device", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("device_bytes", _u64)]
 
 
+class sieve_server_cfg(ctypes.Structure):
+    _fields_ = [("max_requests", ctypes.c_uint32), ("tick_segments", ctypes.c_uint32),
+                ("max_device_bytes", _u64)]
+
+
+class sieve_req(ctypes.Structure):
+    _fields_ = [("lo", _u64), ("hi", _u64), ("kind", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class sieve_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("count", _u64),
+                ("primes", ctypes.POINTER(_u64)), ("latency_us", ctypes.c_double)]
+
+
+class sieve_server_counters(ctypes.Structure):
+    _fields_ = [("submitted", _u64), ("completed", _u64), ("rejected", _u64), ("ticks", _u64),
+                ("integers", _u64), ("in_flight", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("device_bytes_reserved", _u64)]
+
+
+SIEVE_REQ_COUNT = 0
+SIEVE_REQ_LIST = 1
+
 # name -> (restype, argtypes)
 _SIGS = {
     "sieve_create": (_int, [ctypes.POINTER(_vp), _u64, _int, _vp]),
@@ -68,6 +91,12 @@ _SIGS = {
     "sieve_strerror": (ctypes.c_char_p, [_int]),
     "sieve_last_error": (ctypes.c_char_p, [_vp]),
     "sieve_compact_static": (_int, [_vp, _u64, _u64, _vp, _sz, _pu64, _vp]),
+    "sieve_server_create": (_int, [_vp, ctypes.POINTER(sieve_server_cfg), ctypes.POINTER(_vp)]),
+    "sieve_server_submit": (_int, [_vp, ctypes.POINTER(sieve_req), _pu64]),
+    "sieve_server_poll": (_int, [_vp, _u64, ctypes.POINTER(sieve_result), _i64]),
+    "sieve_server_release": (_int, [_vp, _u64]),
+    "sieve_server_stats": (_int, [_vp, ctypes.POINTER(sieve_server_counters)]),
+    "sieve_server_destroy": (None, [_vp]),
 }
 
 _lib = None
@@ -252,6 +281,88 @@ def sieve_crossing_work(ctx: int, lo: int, hi: int) -> int:
 
 def sieve_stream(ctx: int) -> int:
     return load_library().sieve_stream(ctx) or 0
+
+
+def sieve_server_create(ctx: int, max_requests: int = 0, tick_segments: int = 0, max_device_bytes: int = 0) -> int:
+    cfg = sieve_server_cfg(max_requests, tick_segments, max_device_bytes)
+    h = _vp()
+    rc = load_library().sieve_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h))
+    _check(ctx, rc)
+    return h.value
+
+
+def sieve_server_submit(srv: int, lo: int, hi: int, kind: int = SIEVE_REQ_COUNT):
+    """Returns (rc, ticket); rc is SIEVE_OK or SIEVE_EBUSY (other codes raise)."""
+    req = sieve_req(lo, hi, kind, 0)
+    t = _u64()
+    rc = load_library().sieve_server_submit(srv, ctypes.byref(req), ctypes.byref(t))
+    _check(0, rc, allow=(SIEVE_EBUSY,))
+    return rc, t.value
+
+
+def sieve_server_poll(srv: int, ticket: int, timeout_us: int = -1):
+    """Returns (rc, result dict or None); rc SIEVE_OK or SIEVE_ETIMEOUT (others raise).
+    A list result's primes are copied out of the server's memory."""
+    res = sieve_result()
+    rc = load_library().sieve_server_poll(srv, ticket, ctypes.byref(res), timeout_us)
+    _check(0, rc, allow=(SIEVE_ETIMEOUT,))
+    if rc != SIEVE_OK:
+        return rc, None
+    out = {"status": res.status, "kind": res.kind, "count": int(res.count), "latency_us": res.latency_us,
+           "primes": None}
+    if res.kind == SIEVE_REQ_LIST and res.status == SIEVE_OK:
+        import numpy as np
+        n = int(res.count)
+        out["primes"] = (np.ctypeslib.as_array(res.primes, shape=(n,)).copy() if n
+                         else np.zeros(0, dtype=np.uint64))
+    return rc, out
+
+
+def sieve_server_release(srv: int, ticket: int) -> int:
+    rc = load_library().sieve_server_release(srv, ticket)
+    _check(0, rc, allow=(SIEVE_EBUSY, SIEVE_ENOENT))
+    return rc
+
+
+def sieve_server_stats(srv: int) -> dict:
+    c = sieve_server_counters()
+    _check(0, load_library().sieve_server_stats(srv, ctypes.byref(c)))
+    return {k: getattr(c, k) for k, _ in sieve_server_counters._fields_ if k != "reserved"}
+
+
+def sieve_server_destroy(srv: int) -> None:
+    load_library().sieve_server_destroy(srv)
+
+
+class Server:
+    """A continuous-batching request server on a Sieve context."""
+
+    def __init__(self, sieve: "Sieve", max_requests: int = 0, tick_segments: int = 0, max_device_bytes: int = 0):
+        self.sieve = sieve  # keeps the context alive
+        self.srv = sieve_server_create(sieve.ctx, max_requests, tick_segments, max_device_bytes)
+
+    def submit(self, lo, hi, kind=SIEVE_REQ_COUNT):
+        return sieve_server_submit(self.srv, lo, hi, kind)
+
+    def poll(self, ticket, timeout_us=-1):
+        return sieve_server_poll(self.srv, ticket, timeout_us)
+
+    def release(self, ticket):
+        return sieve_server_release(self.srv, ticket)
+
+    def stats(self):
+        return sieve_server_stats(self.srv)
+
+    def close(self):
+        if self.srv:
+            sieve_server_destroy(self.srv)
+            self.srv = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # cudaStreamLegacy: the device's legacy default stream, shared with torch.

@@ -1,0 +1,118 @@
+// host.h -- host-side state shared by the C ABI (sieve_api.cu) and the
+// request server (sieve_server.cu).  Not part of the public interface.
+#pragma once
+
+#include <atomic>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gbsieve.h"
+#include "internal.h"
+
+namespace gbs {
+
+// Launch parameters (copied by the server at creation).
+struct Params {
+    uint32_t seg_bytes = kMaxSegmentBytes;
+    int threads = 1024;
+    uint32_t small_limit = 1792;  // segment bytes / 128
+    int ctas_per_sm = 1;
+    uint32_t chunk_segs = 16;
+    uint64_t bucket_limit = 1ull << 62;  // primes >= this use the bucket lists; 0: the segment size
+};
+
+// Everything one sieve launch reads and writes besides the resident state:
+// a pinned host block and its device copy ([SieveLaunch | RangeDesc x m]),
+// and the accumulators ([0] work counter, [1..m] counts, [m+1] overflow flag).
+struct LaunchBuffers {
+    unsigned char *h_block = nullptr;
+    unsigned char *d_block = nullptr;
+    unsigned long long *d_acc = nullptr;
+    unsigned long long *h_acc = nullptr;  // pinned, [0..m] = counts, overflow
+    size_t cap = 0;                        // ranges
+    RangeDesc *h_ranges() const { return reinterpret_cast<RangeDesc *>(h_block + kLaunchHeader); }
+    RangeDesc *d_ranges() const { return reinterpret_cast<RangeDesc *>(d_block + kLaunchHeader); }
+};
+
+// Scratch of the bitmap -> list compaction.
+struct CompactScratch {
+    uint32_t *counts = nullptr;
+    uint64_t *offsets = nullptr;
+    unsigned long long *d_total = nullptr;
+    unsigned long long *h_total = nullptr;  // pinned
+    size_t cap = 0;                          // tiles
+};
+
+struct BucketStore {
+    uint32_t *d = nullptr;
+    size_t entries = 0;
+    double slack = 1.15;  // capacity = slack x expected hits + 4096, raised on overflow
+};
+
+struct GraphKey {
+    size_t m;
+    int mode;
+    bool operator<(const GraphKey &o) const { return m != o.m ? m < o.m : mode < o.mode; }
+};
+
+}  // namespace gbs
+
+struct sieve_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t capture_stream = nullptr;  // graphs are captured here (never on the legacy stream)
+    uint64_t hi_max = 0;
+    uint64_t prime_limit = 0;
+
+    // resident state: base primes (2 first), their Barrett constants, the pattern tile
+    uint32_t *d_primes = nullptr;
+    uint64_t *d_magic = nullptr;
+    std::vector<uint32_t> h_primes;
+    uint8_t *d_tile = nullptr;
+    uint64_t tile_stride = 0;
+
+    gbs::Params params;
+    gbs::LaunchBuffers lb;
+    gbs::CompactScratch cs;
+    gbs::BucketStore buckets;
+    uint32_t *d_bitmap = nullptr;  // list scratch
+    size_t bitmap_cap = 0;         // words
+
+    // batched launches replayed from graphs, per (ranges, mode); invalidated
+    // when a buffer they reference is reallocated or a parameter changes
+    std::map<gbs::GraphKey, cudaGraphExec_t> graphs;
+
+    std::atomic<uint64_t> device_bytes{0};
+    bool shadow = false;  // a server's private view: resident arrays are borrowed, not owned
+    std::string last_error;
+};
+
+namespace gbs {
+
+int fail(sieve_ctx *c, int code, const std::string &msg);
+int cuda_fail(sieve_ctx *c, cudaError_t e, const char *where);
+uint64_t isqrt64(uint64_t n);
+uint64_t bitmap_words_of(uint64_t lo, uint64_t hi);
+RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_bytes, int mode,
+                     uint32_t *bitmap);
+int alloc_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb, size_t m);
+void free_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb);
+int alloc_compact_scratch(sieve_ctx *ctx, CompactScratch &cs, size_t tiles);
+void free_compact_scratch(sieve_ctx *ctx, CompactScratch &cs);
+
+// Sieve the m ranges lb.h_ranges()[0..m) (planned with plan_range) on
+// `stream`: fills in the launch header, copies the block, clears the
+// accumulators and launches.  Bucket lists are used only if `bs` is given.
+int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
+                  BucketStore *bs);
+
+// Compact the odd-only bitmap of [lo, hi) into out_dev (uint32 or uint64).
+// *n = primes in the range (2 included); SIEVE_ETRUNC if cap < *n.
+// Synchronises `stream`.
+int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
+                 uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64);
+
+}  // namespace gbs

@@ -66,16 +66,21 @@ struct SieveLaunch {
     const uint8_t *tile;                 // kTileCopies shifted copies of the pattern
     uint64_t tile_stride;                // bytes between copies
     uint32_t seg_bytes;                  // S, multiple of 32, <= kMaxSegmentBytes
-    int threads;                         // 256, 512 or 1024
-    int grid;                            // persistent CTAs
 };
+// Bytes reserved for the SieveLaunch at the head of a launch block; the
+// RangeDescs follow it.
+constexpr size_t kLaunchHeader = 256;
+static_assert(sizeof(SieveLaunch) <= kLaunchHeader, "launch header");
 
 // Kernel launchers (sieve_kernels.cu).  All enqueue on `stream` and return the
 // CUDA launch status.
 cudaError_t launch_build_tile(uint8_t *tile, uint64_t stride, uint32_t len, cudaStream_t stream);
 cudaError_t launch_tiny_primes(uint32_t *out, uint32_t *n_out, cudaStream_t stream);
 cudaError_t launch_magic(const uint32_t *primes, uint64_t *magic, uint64_t n, cudaStream_t stream);
-cudaError_t launch_sieve(int mode, const SieveLaunch &L, cudaStream_t stream);
+// Launch parameters live in device memory (d_launch) so that a captured graph
+// can be replayed with new ranges; d_launch->n_items may be 0.
+cudaError_t launch_sieve(int mode, const SieveLaunch *d_launch, int grid, int threads, uint32_t seg_bytes,
+                         cudaStream_t stream);
 cudaError_t set_sieve_smem_limits();
 
 // Compaction of an odd-only bitmap into a prime list.

@@ -1,5 +1,6 @@
 // sieve_api.cu -- host side of gbsieve: the context (resident base primes,
-// pattern tile, scratch), range planning and the C ABI of include/gbsieve.h.
+// pattern tile, scratch), range planning, launches and the C ABI of
+// include/gbsieve.h.
 //
 // Base primes (Section 1's sqrt bound) are made on the device in three
 // rounds, each using the sieve itself: primes < 256 by trial division, then
@@ -11,68 +12,26 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
-#include "gbsieve.h"
-#include "internal.h"
+#include "host.h"
 
 using namespace gbs;
 
-struct sieve_ctx {
-    int device = 0;
-    int num_sms = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    uint64_t hi_max = 0;
-    uint64_t prime_limit = 0;
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+    } while (0)
 
-    // resident state
-    uint32_t *d_primes = nullptr;
-    uint64_t *d_magic = nullptr;
-    uint64_t n_primes = 0;
-    std::vector<uint32_t> h_primes;
-    uint8_t *d_tile = nullptr;
-    uint64_t tile_stride = 0;
-
-    // per-launch buffers: [0] item counter, [1..] per-range counts
-    unsigned long long *d_acc = nullptr;
-    size_t acc_cap = 0;  // ranges
-    RangeDesc *d_ranges = nullptr;
-    RangeDesc *h_ranges = nullptr;  // pinned
-    unsigned long long *h_acc = nullptr;  // pinned
-    size_t ranges_cap = 0;
-
-    // compaction scratch
-    uint32_t *d_bitmap = nullptr;
-    size_t bitmap_cap = 0;  // words
-    uint32_t *d_tile_counts = nullptr;
-    uint64_t *d_tile_offsets = nullptr;
-    size_t tiles_cap = 0;
-
-    // bucket lists for the large primes (grid x chunk x cap entries)
-    uint32_t *d_buckets = nullptr;
-    size_t buckets_entries = 0;
-    double bucket_slack = 1.15;  // capacity = slack x expected hits + 4096, raised on overflow
-
-    // launch parameters
-    uint32_t seg_bytes = kMaxSegmentBytes;
-    int threads = 1024;
-    uint32_t small_limit = 1792;  // segment bytes / 128
-    int ctas_per_sm = 1;
-    uint32_t chunk_segs = 16;
-    uint64_t bucket_limit = 1ull << 62;  // primes >= this use the bucket lists; 0: the segment size
-
-    uint64_t device_bytes = 0;
-    std::string last_error;
-};
+namespace gbs {
 
 namespace {
-
 const char *kNames[] = {"ok", "invalid argument", "range exceeds limit", "output truncated",
                         "out of memory", "CUDA error", "timed out", "busy", "unknown ticket",
                         "device-side limit hit"};
+}  // namespace
 
 int fail(sieve_ctx *c, int code, const std::string &msg) {
     if (c) c->last_error = msg;
@@ -80,16 +39,11 @@ int fail(sieve_ctx *c, int code, const std::string &msg) {
 }
 
 int cuda_fail(sieve_ctx *c, cudaError_t e, const char *where) {
+    cudaGetLastError();  // clear a non-sticky launch error
     std::string m = std::string(where) + ": " + cudaGetErrorString(e);
     if (e == cudaErrorMemoryAllocation) return fail(c, SIEVE_ENOMEM, m);
     return fail(c, SIEVE_ECUDA, m);
 }
-
-#define CK(call)                                                  \
-    do {                                                          \
-        cudaError_t _e = (call);                                  \
-        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
-    } while (0)
 
 uint64_t isqrt64(uint64_t n) {
     uint64_t r = 0, bit = 1ull << 62;
@@ -113,6 +67,8 @@ uint64_t bitmap_words_of(uint64_t lo, uint64_t hi) {
     return (nbits + 31) / 32;
 }
 
+namespace {
+
 // Number of base primes p with p * p < hi, i.e. p <= floor(sqrt(hi - 1)).
 uint32_t primes_needed(const std::vector<uint32_t> &primes, uint64_t hi) {
     if (hi < 2) return 0;
@@ -122,14 +78,18 @@ uint32_t primes_needed(const std::vector<uint32_t> &primes, uint64_t hi) {
                       primes.begin());
 }
 
+// Index of the first prime >= limit, at least the first crossing prime.
+uint32_t first_at_least(const std::vector<uint32_t> &primes, uint64_t limit) {
+    if (limit > 0xffffffffull) return (uint32_t)primes.size();
+    uint32_t e = (uint32_t)(std::lower_bound(primes.begin(), primes.end(), (uint32_t)limit) - primes.begin());
+    return std::max<uint32_t>(e, kFirstCrossingPrime);
+}
+
 template <typename T>
 int dev_alloc(sieve_ctx *ctx, T **p, size_t count) {
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return cuda_fail(ctx, e, "cudaMalloc");
-    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
     *p = static_cast<T *>(q);
     ctx->device_bytes += std::max<size_t>(count, 1) * sizeof(T);
     return SIEVE_OK;
@@ -144,53 +104,67 @@ void dev_free(sieve_ctx *ctx, T *&p, size_t count) {
     p = nullptr;
 }
 
-int ensure_ranges(sieve_ctx *ctx, size_t m) {
-    if (m <= ctx->ranges_cap) return SIEVE_OK;
-    size_t cap = std::max<size_t>(m, 64);
-    dev_free(ctx, ctx->d_ranges, ctx->ranges_cap);
-    dev_free(ctx, ctx->d_acc, ctx->acc_cap + 2);
-    if (ctx->h_ranges) cudaFreeHost(ctx->h_ranges);
-    if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
-    ctx->h_ranges = nullptr;
-    ctx->h_acc = nullptr;
-    ctx->ranges_cap = ctx->acc_cap = 0;
-    int rc = dev_alloc(ctx, &ctx->d_ranges, cap);
+void drop_graphs(sieve_ctx *ctx) {
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);
+    ctx->graphs.clear();
+}
+
+}  // namespace
+
+int alloc_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb, size_t m) {
+    if (m <= lb.cap) return SIEVE_OK;
+    free_launch_buffers(ctx, lb);
+    const size_t cap = std::max<size_t>(m, 64);
+    const size_t block = kLaunchHeader + cap * sizeof(RangeDesc);
+    int rc = dev_alloc(ctx, &lb.d_block, block);
     if (rc) return rc;
-    rc = dev_alloc(ctx, &ctx->d_acc, cap + 2);
+    rc = dev_alloc(ctx, &lb.d_acc, cap + 2);
     if (rc) return rc;
-    CK(cudaMallocHost(&ctx->h_ranges, cap * sizeof(RangeDesc)));
-    CK(cudaMallocHost(&ctx->h_acc, (cap + 2) * sizeof(unsigned long long)));
-    ctx->ranges_cap = ctx->acc_cap = cap;
+    CK(cudaMallocHost(&lb.h_block, block));
+    CK(cudaMallocHost(&lb.h_acc, (cap + 2) * sizeof(unsigned long long)));
+    lb.cap = cap;
     return SIEVE_OK;
 }
 
-int ensure_bitmap(sieve_ctx *ctx, size_t words) {
-    if (words <= ctx->bitmap_cap) return SIEVE_OK;
-    dev_free(ctx, ctx->d_bitmap, ctx->bitmap_cap);
-    ctx->bitmap_cap = 0;
-    int rc = dev_alloc(ctx, &ctx->d_bitmap, words);
+void free_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb) {
+    const size_t block = kLaunchHeader + lb.cap * sizeof(RangeDesc);
+    if (lb.d_block) dev_free(ctx, lb.d_block, block);
+    if (lb.d_acc) dev_free(ctx, lb.d_acc, lb.cap + 2);
+    if (lb.h_block) cudaFreeHost(lb.h_block);
+    if (lb.h_acc) cudaFreeHost(lb.h_acc);
+    lb = LaunchBuffers();
+}
+
+int alloc_compact_scratch(sieve_ctx *ctx, CompactScratch &cs, size_t tiles) {
+    if (!cs.d_total) {
+        int rc = dev_alloc(ctx, &cs.d_total, 1);
+        if (rc) return rc;
+        CK(cudaMallocHost(&cs.h_total, sizeof(unsigned long long)));
+    }
+    if (tiles <= cs.cap) return SIEVE_OK;
+    dev_free(ctx, cs.counts, cs.cap);
+    dev_free(ctx, cs.offsets, cs.cap);
+    cs.cap = 0;
+    int rc = dev_alloc(ctx, &cs.counts, tiles);
     if (rc) return rc;
-    ctx->bitmap_cap = words;
+    rc = dev_alloc(ctx, &cs.offsets, tiles);
+    if (rc) return rc;
+    cs.cap = tiles;
     return SIEVE_OK;
 }
 
-int ensure_tiles(sieve_ctx *ctx, size_t ntiles) {
-    if (ntiles <= ctx->tiles_cap) return SIEVE_OK;
-    dev_free(ctx, ctx->d_tile_counts, ctx->tiles_cap);
-    dev_free(ctx, ctx->d_tile_offsets, ctx->tiles_cap);
-    ctx->tiles_cap = 0;
-    int rc = dev_alloc(ctx, &ctx->d_tile_counts, ntiles);
-    if (rc) return rc;
-    rc = dev_alloc(ctx, &ctx->d_tile_offsets, ntiles);
-    if (rc) return rc;
-    ctx->tiles_cap = ntiles;
-    return SIEVE_OK;
+void free_compact_scratch(sieve_ctx *ctx, CompactScratch &cs) {
+    dev_free(ctx, cs.counts, cs.cap);
+    dev_free(ctx, cs.offsets, cs.cap);
+    dev_free(ctx, cs.d_total, 1);
+    if (cs.h_total) cudaFreeHost(cs.h_total);
+    cs = CompactScratch();
 }
 
-// Fill one RangeDesc (item_first is set by the caller).  Segments start at a
-// wheel byte Bbase with 30 Bbase <= lo and 30 Bbase + 1 = (lo | 1) (mod 64).
-RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_bytes,
-                     int mode, uint32_t *bitmap) {
+// Fill one RangeDesc (item_first is set at launch).  Segments start at a wheel
+// byte Bbase with 30 Bbase <= lo and 30 Bbase + 1 = (lo | 1) (mod 64).
+RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_bytes, int mode,
+                     uint32_t *bitmap) {
     RangeDesc r;
     std::memset(&r, 0, sizeof r);
     r.lo = lo;
@@ -216,174 +190,186 @@ RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t 
     return r;
 }
 
-uint32_t small_end_for(const std::vector<uint32_t> &primes, uint32_t limit) {
-    uint32_t e = (uint32_t)(std::lower_bound(primes.begin(), primes.end(), limit) - primes.begin());
-    return std::max<uint32_t>(e, kFirstCrossingPrime);
-}
-
-// Run the sieve over ranges h_ranges[0..m) already planned (item_first set
-// here).  Layout of ctx->d_acc: [0] work counter, [1..m] per-range counts,
-// [m+1] bucket-overflow flag.  No synchronisation.
-int run_sieve(sieve_ctx *ctx, int mode, const std::vector<uint32_t> &h, const uint32_t *primes_dev,
-              const uint64_t *magic_dev, size_t m) {
+int prepare_launch(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t m, BucketStore *bs,
+                   uint64_t *items_out) {
+    const std::vector<uint32_t> &h = ctx->h_primes;
+    RangeDesc *rd = lb.h_ranges();
     uint64_t segs = 0;
     uint32_t nmax = 0;
     for (size_t i = 0; i < m; ++i) {
-        segs += ctx->h_ranges[i].nseg;
-        if (ctx->h_ranges[i].nseg) nmax = std::max(nmax, ctx->h_ranges[i].n_use);
+        segs += rd[i].nseg;
+        if (rd[i].nseg) nmax = std::max(nmax, rd[i].n_use);
     }
-    const uint64_t grid_max = (uint64_t)ctx->num_sms * ctx->ctas_per_sm;
-    const uint32_t mid_end = std::max<uint32_t>(small_end_for(h, ctx->small_limit),
-                                                small_end_for(h, std::max<uint32_t>(ctx->seg_bytes / 8, 23)));
-    const uint64_t blim = ctx->bucket_limit ? ctx->bucket_limit : ctx->seg_bytes;
-    const uint32_t bfirst = std::max(blim > 0xffffffffull ? (uint32_t)h.size() : small_end_for(h, (uint32_t)blim),
-                                     mid_end);
-    const bool buckets = bfirst < nmax;
+    const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
+    const uint32_t small_end = first_at_least(h, prm.small_limit);
+    // primes below S / 8 have at least 8 hits per progression in a full segment
+    const uint32_t mid_end = std::max(small_end, first_at_least(h, std::max<uint32_t>(prm.seg_bytes / 8, 23)));
+    const uint64_t blim = prm.bucket_limit ? prm.bucket_limit : prm.seg_bytes;
+    const uint32_t bfirst = std::max(first_at_least(h, blim), mid_end);
+    const bool buckets = bs && bfirst < nmax;
     // Chunks (several segments per work item) only pay off with bucket lists;
     // keep at least 4 items per CTA so the last wave stays short.
     uint32_t C = 1;
     if (buckets) {
-        C = ctx->chunk_segs;
-        while (C > 1 && segs / C < 4 * grid_max) C /= 2;
+        C = prm.chunk_segs;
+        while (C > 1 && segs / C < 4 * grid) C /= 2;
     }
     uint64_t items = 0;
     for (size_t i = 0; i < m; ++i) {
-        ctx->h_ranges[i].item_first = items;
-        items += (ctx->h_ranges[i].nseg + C - 1) / C;
+        rd[i].item_first = items;
+        items += (rd[i].nseg + C - 1) / C;
     }
-    CK(cudaMemcpyAsync(ctx->d_ranges, ctx->h_ranges, m * sizeof(RangeDesc), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_acc, 0, (m + 2) * sizeof(unsigned long long), ctx->stream));
-    SieveLaunch L;
+    SieveLaunch &L = *reinterpret_cast<SieveLaunch *>(lb.h_block);
     std::memset(&L, 0, sizeof L);
-    L.ranges = ctx->d_ranges;
+    L.ranges = lb.d_ranges();
     L.n_ranges = (uint32_t)m;
     L.n_items = items;
-    L.item_counter = ctx->d_acc;
-    L.counts = ctx->d_acc + 1;
-    L.overflow = reinterpret_cast<unsigned *>(ctx->d_acc + m + 1);
-    L.primes = primes_dev;
-    L.magic = magic_dev;
+    L.item_counter = lb.d_acc;
+    L.counts = lb.d_acc + 1;
+    L.overflow = reinterpret_cast<unsigned *>(lb.d_acc + m + 1);
+    L.primes = ctx->d_primes;
+    L.magic = ctx->d_magic;
     L.tile = ctx->d_tile;
     L.tile_stride = ctx->tile_stride;
-    L.seg_bytes = ctx->seg_bytes;
-    L.threads = ctx->threads;
+    L.seg_bytes = prm.seg_bytes;
     L.chunk_segs = C;
-    L.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(grid_max, items));
-    L.small_end = small_end_for(h, ctx->small_limit);
-    // primes below S / 8 have at least 8 hits per progression in a full segment
+    L.small_end = small_end;
     L.mid_end = mid_end;
-    // primes from the bucket limit up go through the per-segment bucket lists
     L.bucket_first = 0xffffffffu;
     if (buckets) {
-        // expected hits per full segment: 8 S / p per bucket prime (one per wheel class
-        // with probability S / p); the list capacity is that with a margin
+        // expected hits per full segment: 8 S / p per bucket prime (one per wheel
+        // class with probability S / p); the list capacity is that with a margin
         double e = 0;
-        for (uint32_t i = bfirst; i < nmax; ++i) e += 8.0 * ctx->seg_bytes / h[i];
-        uint64_t cap = (uint64_t)(ctx->bucket_slack * e) + 4096;
+        for (uint32_t i = bfirst; i < nmax; ++i) e += 8.0 * prm.seg_bytes / h[i];
+        uint64_t cap = (uint64_t)(bs->slack * e) + 4096;
         cap = (cap + 31) & ~31ull;
-        const size_t need = (size_t)L.grid * C * cap;
-        if (need > ctx->buckets_entries) {
-            dev_free(ctx, ctx->d_buckets, ctx->buckets_entries);
-            ctx->buckets_entries = 0;
-            int rc = dev_alloc(ctx, &ctx->d_buckets, need);
+        const size_t need = (size_t)grid * C * cap;
+        if (need > bs->entries) {
+            dev_free(ctx, bs->d, bs->entries);
+            bs->entries = 0;
+            int rc = dev_alloc(ctx, &bs->d, need);
             if (rc) return rc;
-            ctx->buckets_entries = need;
+            bs->entries = need;
         }
         L.bucket_first = bfirst;
-        L.buckets = ctx->d_buckets;
+        L.buckets = bs->d;
         L.bucket_cap = (uint32_t)cap;
     }
-    CK(launch_sieve(mode, L, ctx->stream));
+    *items_out = items;
     return SIEVE_OK;
 }
 
-// Copy the m counts and the overflow flag to ctx->h_acc and wait.  Returns 1
-// if a bucket list overflowed (the results are then invalid), 0 if not.
-int finish_sieve(sieve_ctx *ctx, size_t m, int *overflowed) {
-    CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc + 1, (m + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    *overflowed = (ctx->h_acc[m] & 0xffffffffull) != 0;
+int enqueue_launch(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
+                   int grid) {
+    const size_t block = kLaunchHeader + m * sizeof(RangeDesc);
+    CK(cudaMemcpyAsync(lb.d_block, lb.h_block, block, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
+    if (grid > 0)
+        CK(launch_sieve(mode, reinterpret_cast<const SieveLaunch *>(lb.d_block), grid, prm.threads, prm.seg_bytes,
+                        stream));
     return SIEVE_OK;
 }
 
-// run_sieve + finish_sieve, re-running with larger bucket lists if one
-// overflowed (never expected: the margin is far above the spread of the hit
-// counts).  Counts are left in ctx->h_acc[0..m).
-int run_sieve_sync(sieve_ctx *ctx, int mode, size_t m) {
-    for (int attempt = 0; attempt < 4; ++attempt) {
-        int rc = run_sieve(ctx, mode, ctx->h_primes, ctx->d_primes, ctx->d_magic, m);
-        if (rc) return rc;
-        int of = 0;
-        rc = finish_sieve(ctx, m, &of);
-        if (rc) return rc;
-        if (!of) return SIEVE_OK;
-        ctx->bucket_slack *= 2;
-    }
-    return fail(ctx, SIEVE_EDEVICE, "bucket lists overflowed repeatedly");
+int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
+                  BucketStore *bs) {
+    uint64_t items = 0;
+    int rc = prepare_launch(ctx, prm, lb, m, bs, &items);
+    if (rc) return rc;
+    const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
+    return enqueue_launch(ctx, stream, prm, mode, lb, m, (int)std::min<uint64_t>(grid, items));
 }
 
-// Compact the odd-only bitmap of [lo, hi) at bitmap_dev into out_dev (uint32 or
-// uint64 values).  *n = number of primes (2 included).
-int compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo, uint64_t hi, void *out_dev, size_t cap,
-            uint64_t *n, int out64) {
+int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
+                 uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64) {
     const uint64_t nwords = bitmap_words_of(lo, hi);
     const uint32_t two = (lo <= 2 && 2 < hi) ? 1 : 0;
     const uint64_t ntiles = (nwords + kCompactTileWords - 1) / kCompactTileWords;
+    int rc = alloc_compact_scratch(ctx, cs, ntiles);
+    if (rc) return rc;
     uint64_t total = 0;
+    const int grid = ctx->num_sms * 8;
     if (ntiles) {
-        int rc = ensure_tiles(ctx, ntiles);
-        if (rc) return rc;
-        int grid = ctx->num_sms * 8;
-        CK(launch_tile_popc(bitmap_dev, nwords, ctx->d_tile_counts, ntiles, grid, ctx->stream));
-        CK(launch_tile_scan(ctx->d_tile_counts, ctx->d_tile_offsets, ntiles, ctx->d_acc, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-        total = ctx->h_acc[0];
+        CK(launch_tile_popc(bitmap_dev, nwords, cs.counts, ntiles, grid, stream));
+        CK(launch_tile_scan(cs.counts, cs.offsets, ntiles, cs.d_total, stream));
+        CK(cudaMemcpyAsync(cs.h_total, cs.d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        total = *cs.h_total;
     }
     *n = total + two;
     if (*n > cap) return fail(ctx, SIEVE_ETRUNC, "output capacity below the prime count");
     if (*n == 0) return SIEVE_OK;
     if (!out_dev) return fail(ctx, SIEVE_EINVAL, "null output");
-    if (two) CK(launch_put_two(out_dev, out64, ctx->stream));
-    if (ntiles) {
-        int grid = ctx->num_sms * 8;
-        CK(launch_emit(bitmap_dev, nwords, ctx->d_tile_offsets, ntiles, lo | 1, two, out_dev, out64, grid,
-                       ctx->stream));
-    }
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (two) CK(launch_put_two(out_dev, out64, stream));
+    if (ntiles) CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, lo | 1, two, out_dev, out64, grid, stream));
+    CK(cudaStreamSynchronize(stream));
     return SIEVE_OK;
 }
 
-// Sieve [0, limit + 1) into the scratch bitmap and compact it into a fresh
-// device array of primes, using the base primes (primes_dev, magic_dev,
-// host copy h) that cover sqrt(limit).
-int primes_upto(sieve_ctx *ctx, uint64_t limit, const std::vector<uint32_t> &h, const uint32_t *primes_dev,
-                const uint64_t *magic_dev, uint32_t **out_dev, std::vector<uint32_t> &out_h) {
+}  // namespace gbs
+
+namespace {
+
+// Copy the m counts and the overflow flag to lb.h_acc and wait; *overflowed = 1
+// if a bucket list overflowed (the results are then invalid).
+int finish(sieve_ctx *ctx, LaunchBuffers &lb, size_t m, int *overflowed) {
+    CK(cudaMemcpyAsync(lb.h_acc, lb.d_acc + 1, (m + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *overflowed = (lb.h_acc[m] & 0xffffffffull) != 0;
+    return SIEVE_OK;
+}
+
+// launch + finish on the context's stream, re-running with larger bucket lists
+// if one overflowed (never expected: the margin is far above the spread of the
+// hit counts).  Counts are left in ctx->lb.h_acc[0..m).
+int run_sync(sieve_ctx *ctx, int mode, size_t m) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        int rc = launch_ranges(ctx, ctx->stream, ctx->params, mode, ctx->lb, m, &ctx->buckets);
+        if (rc) return rc;
+        int of = 0;
+        rc = finish(ctx, ctx->lb, m, &of);
+        if (rc) return rc;
+        if (!of) return SIEVE_OK;
+        ctx->buckets.slack *= 2;
+    }
+    return fail(ctx, SIEVE_EDEVICE, "bucket lists overflowed repeatedly");
+}
+
+int ensure_bitmap(sieve_ctx *ctx, size_t words) {
+    if (words <= ctx->bitmap_cap) return SIEVE_OK;
+    dev_free(ctx, ctx->d_bitmap, ctx->bitmap_cap);
+    ctx->bitmap_cap = 0;
+    int rc = dev_alloc(ctx, &ctx->d_bitmap, words);
+    if (rc) return rc;
+    ctx->bitmap_cap = words;
+    return SIEVE_OK;
+}
+
+int ensure_launch(sieve_ctx *ctx, size_t m) {
+    if (m <= ctx->lb.cap) return SIEVE_OK;
+    drop_graphs(ctx);  // they reference the old buffers
+    return alloc_launch_buffers(ctx, ctx->lb, m);
+}
+
+// Sieve [0, limit + 1) into the scratch bitmap with the current base primes
+// (they cover sqrt(limit)) and compact it into a fresh device array.
+int primes_upto(sieve_ctx *ctx, uint64_t limit, uint32_t **out_dev, std::vector<uint32_t> &out_h) {
     const uint64_t hi = limit + 1;
-    int rc = ensure_ranges(ctx, 1);
+    int rc = ensure_launch(ctx, 1);
     if (rc) return rc;
     rc = ensure_bitmap(ctx, bitmap_words_of(0, hi));
     if (rc) return rc;
-    ctx->h_ranges[0] = plan_range(h, 0, hi, ctx->seg_bytes, kModeBitmap, ctx->d_bitmap);
-    for (int attempt = 0;; ++attempt) {
-        rc = run_sieve(ctx, kModeBitmap, h, primes_dev, magic_dev, 1);
-        if (rc) return rc;
-        int of = 0;
-        rc = finish_sieve(ctx, 1, &of);
-        if (rc) return rc;
-        if (!of) break;
-        if (attempt == 3) return fail(ctx, SIEVE_EDEVICE, "bucket lists overflowed repeatedly");
-        ctx->bucket_slack *= 2;
-    }
+    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, 0, hi, ctx->params.seg_bytes, kModeBitmap, ctx->d_bitmap);
+    rc = run_sync(ctx, kModeBitmap, 1);
+    if (rc) return rc;
     uint64_t n = 0;
-    rc = compact(ctx, ctx->d_bitmap, 0, hi, nullptr, 0, &n, 0);
+    rc = compact_with(ctx, ctx->stream, ctx->cs, ctx->d_bitmap, 0, hi, nullptr, 0, &n, 0);
     if (rc != SIEVE_ETRUNC && rc != SIEVE_OK) return rc;
     uint32_t *d = nullptr;
     rc = dev_alloc(ctx, &d, n);
     if (rc) return rc;
     uint64_t n2 = 0;
-    rc = compact(ctx, ctx->d_bitmap, 0, hi, d, n, &n2, 0);
+    rc = compact_with(ctx, ctx->stream, ctx->cs, ctx->d_bitmap, 0, hi, d, n, &n2, 0);
     if (rc) {
         dev_free(ctx, d, n);
         return rc;
@@ -405,43 +391,38 @@ int make_base_primes(sieve_ctx *ctx) {
     uint32_t ntiny = 0;
     CK(cudaMemcpyAsync(&ntiny, d_ntiny, sizeof ntiny, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    std::vector<uint32_t> h(ntiny);
-    CK(cudaMemcpy(h.data(), d_tiny, ntiny * sizeof(uint32_t), cudaMemcpyDeviceToHost));
     dev_free(ctx, d_ntiny, 1);
-    uint32_t *d_cur = d_tiny;
+    ctx->h_primes.resize(ntiny);
+    CK(cudaMemcpy(ctx->h_primes.data(), d_tiny, ntiny * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    ctx->d_primes = d_tiny;
     size_t cur_n = 64;
-    uint64_t *d_mag = nullptr;
-    rc = dev_alloc(ctx, &d_mag, cur_n);
+    rc = dev_alloc(ctx, &ctx->d_magic, cur_n);
     if (rc) return rc;
-    CK(launch_magic(d_cur, d_mag, h.size(), ctx->stream));
+    CK(launch_magic(ctx->d_primes, ctx->d_magic, ctx->h_primes.size(), ctx->stream));
 
     // rounds 2 and 3
     const uint64_t stages[2] = {std::min<uint64_t>(ctx->prime_limit, 65535), ctx->prime_limit};
     for (int st = 0; st < 2; ++st) {
         const uint64_t lim = stages[st];
-        if (!h.empty() && h.back() >= lim) break;
+        if (!ctx->h_primes.empty() && ctx->h_primes.back() >= lim) break;
         if (st == 1 && lim <= 65535) break;
         uint32_t *d_next = nullptr;
         std::vector<uint32_t> h_next;
-        rc = primes_upto(ctx, lim, h, d_cur, d_mag, &d_next, h_next);
+        rc = primes_upto(ctx, lim, &d_next, h_next);
         if (rc) return rc;
-        dev_free(ctx, d_cur, cur_n);
-        dev_free(ctx, d_mag, cur_n);
-        d_cur = d_next;
+        dev_free(ctx, ctx->d_primes, cur_n);
+        dev_free(ctx, ctx->d_magic, cur_n);
+        ctx->d_primes = d_next;
         cur_n = h_next.size();
-        h.swap(h_next);
-        rc = dev_alloc(ctx, &d_mag, cur_n);
+        ctx->h_primes.swap(h_next);
+        rc = dev_alloc(ctx, &ctx->d_magic, cur_n);
         if (rc) return rc;
-        CK(launch_magic(d_cur, d_mag, h.size(), ctx->stream));
+        CK(launch_magic(ctx->d_primes, ctx->d_magic, ctx->h_primes.size(), ctx->stream));
     }
     // keep primes <= prime_limit
-    size_t keep = std::upper_bound(h.begin(), h.end(), (uint32_t)std::min<uint64_t>(ctx->prime_limit, 0xffffffffu)) -
-                  h.begin();
-    h.resize(keep);
-    ctx->d_primes = d_cur;
-    ctx->d_magic = d_mag;
-    ctx->n_primes = h.size();
-    ctx->h_primes.swap(h);
+    std::vector<uint32_t> &h = ctx->h_primes;
+    h.resize(std::upper_bound(h.begin(), h.end(), (uint32_t)std::min<uint64_t>(ctx->prime_limit, 0xffffffffu)) -
+             h.begin());
     CK(cudaStreamSynchronize(ctx->stream));
     return SIEVE_OK;
 }
@@ -458,13 +439,59 @@ int set_device(sieve_ctx *ctx) {
     return SIEVE_OK;
 }
 
-int sieve_bitmap_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, uint64_t *count) {
-    int rc = ensure_ranges(ctx, 1);
+int bitmap_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, uint64_t *count) {
+    int rc = ensure_launch(ctx, 1);
     if (rc) return rc;
-    ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeBitmap, out_dev);
-    rc = run_sieve_sync(ctx, kModeBitmap, 1);
+    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeBitmap, out_dev);
+    rc = run_sync(ctx, kModeBitmap, 1);
     if (rc) return rc;
-    if (count) *count = ctx->h_acc[0];
+    if (count) *count = ctx->lb.h_acc[0];
+    return SIEVE_OK;
+}
+
+// A batched launch replayed from a CUDA graph captured once per (ranges, mode):
+// block copy, accumulator clear, the persistent sieve kernel over the full
+// grid (CTAs without work exit at once) and the copy-back of the counts.  The
+// launch parameters and range descriptors live in the pinned block that the
+// graph's first copy reads, so a replay only needs the block refreshed.
+// Batches that need bucket lists are launched directly (*used = false).
+int batch_graph(sieve_ctx *ctx, int mode, size_t m, bool *used) {
+    *used = false;
+    const Params &prm = ctx->params;
+    uint64_t items = 0;
+    int rc = prepare_launch(ctx, prm, ctx->lb, m, nullptr, &items);
+    if (rc) return rc;
+    {
+        const uint64_t blim = prm.bucket_limit ? prm.bucket_limit : prm.seg_bytes;
+        uint32_t nmax = 0;
+        for (size_t i = 0; i < m; ++i)
+            if (ctx->lb.h_ranges()[i].nseg) nmax = std::max(nmax, ctx->lb.h_ranges()[i].n_use);
+        if (first_at_least(ctx->h_primes, blim) < nmax) return SIEVE_OK;
+    }
+    if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    const GraphKey key{m, mode};
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        const int grid = ctx->num_sms * prm.ctas_per_sm;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_launch(ctx, ctx->capture_stream, prm, mode, ctx->lb, m, grid);
+        cudaError_t e1 = cudaMemcpyAsync(ctx->lb.h_acc, ctx->lb.d_acc + 1, (m + 1) * sizeof(unsigned long long),
+                                         cudaMemcpyDeviceToHost, ctx->capture_stream);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
+        if (rc || e1 != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : cuda_fail(ctx, e1 != cudaSuccess ? e1 : e2, "graph capture");
+        }
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e3 = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e3 != cudaSuccess) return cuda_fail(ctx, e3, "cudaGraphInstantiate");
+        it = ctx->graphs.emplace(key, ex).first;
+    }
+    CK(cudaGraphLaunch(it->second, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *used = true;
     return SIEVE_OK;
 }
 
@@ -493,35 +520,30 @@ int sieve_create(sieve_ctx **out, uint64_t hi_max, int device, void *cuda_stream
     ctx->device = device;
     ctx->hi_max = hi_max;
     ctx->prime_limit = isqrt64(hi_max - 1);
-    int rc = SIEVE_OK;
     auto bail = [&](int code) {
         sieve_destroy(ctx);
         return code;
     };
-    {
-        cudaError_t e = cudaSetDevice(device);
-        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaSetDevice"));
-        e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaDeviceGetAttribute"));
-        if (cuda_stream) {
-            ctx->stream = static_cast<cudaStream_t>(cuda_stream);
-        } else {
-            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
-            if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaStreamCreate"));
-            ctx->own_stream = true;
-        }
-        e = set_sieve_smem_limits();
-        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaFuncSetAttribute"));
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaSetDevice"));
+    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaDeviceGetAttribute"));
+    if (cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaStreamCreate"));
+        ctx->own_stream = true;
     }
+    e = set_sieve_smem_limits();
+    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaFuncSetAttribute"));
     // pattern tile: 16 copies, each long enough for any phase plus a full segment
     const uint64_t len = ((uint64_t)kTilePeriod + kMaxSegmentBytes + 32 + 15) & ~15ull;
     ctx->tile_stride = len;
-    rc = dev_alloc(ctx, &ctx->d_tile, len * kTileCopies);
+    int rc = dev_alloc(ctx, &ctx->d_tile, len * kTileCopies);
     if (rc) return bail(rc);
-    {
-        cudaError_t e = launch_build_tile(ctx->d_tile, ctx->tile_stride, (uint32_t)len, ctx->stream);
-        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "build tile"));
-    }
+    e = launch_build_tile(ctx->d_tile, ctx->tile_stride, (uint32_t)len, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "build tile"));
     rc = make_base_primes(ctx);
     if (rc) return bail(rc);
     *out = ctx;
@@ -532,17 +554,17 @@ void sieve_destroy(sieve_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    cudaFree(ctx->d_primes);
-    cudaFree(ctx->d_magic);
-    cudaFree(ctx->d_tile);
-    cudaFree(ctx->d_acc);
-    cudaFree(ctx->d_ranges);
+    drop_graphs(ctx);
+    if (!ctx->shadow) {
+        cudaFree(ctx->d_primes);
+        cudaFree(ctx->d_magic);
+        cudaFree(ctx->d_tile);
+    }
     cudaFree(ctx->d_bitmap);
-    cudaFree(ctx->d_tile_counts);
-    cudaFree(ctx->d_tile_offsets);
-    cudaFree(ctx->d_buckets);
-    if (ctx->h_ranges) cudaFreeHost(ctx->h_ranges);
-    if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
+    cudaFree(ctx->buckets.d);
+    free_launch_buffers(ctx, ctx->lb);
+    free_compact_scratch(ctx, ctx->cs);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -556,12 +578,12 @@ int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count) {
         *count = 0;
         return SIEVE_OK;
     }
-    rc = ensure_ranges(ctx, 1);
+    rc = ensure_launch(ctx, 1);
     if (rc) return rc;
-    ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeCount, nullptr);
-    rc = run_sieve_sync(ctx, kModeCount, 1);
+    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeCount, nullptr);
+    rc = run_sync(ctx, kModeCount, 1);
     if (rc) return rc;
-    *count = ctx->h_acc[0];
+    *count = ctx->lb.h_acc[0];
     return SIEVE_OK;
 }
 
@@ -570,13 +592,13 @@ int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_de
     int rc = check_range(ctx, lo, hi);
     if (rc) return rc;
     if ((rc = set_device(ctx))) return rc;
-    rc = ensure_ranges(ctx, 1);
+    rc = ensure_launch(ctx, 1);
     if (rc) return rc;
-    ctx->h_ranges[0] = plan_range(ctx->h_primes, lo, hi, ctx->seg_bytes, kModeCount, nullptr);
-    rc = run_sieve(ctx, kModeCount, ctx->h_primes, ctx->d_primes, ctx->d_magic, 1);
+    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeCount, nullptr);
+    rc = launch_ranges(ctx, ctx->stream, ctx->params, kModeCount, ctx->lb, 1, &ctx->buckets);
     if (rc) return rc;
     // the count, or UINT64_MAX if a bucket list overflowed
-    CK(launch_finalize_count(ctx->d_acc + 1, reinterpret_cast<const unsigned *>(ctx->d_acc + 2), count_dev,
+    CK(launch_finalize_count(ctx->lb.d_acc + 1, reinterpret_cast<const unsigned *>(ctx->lb.d_acc + 2), count_dev,
                              ctx->stream));
     return SIEVE_OK;
 }
@@ -592,7 +614,7 @@ int sieve_bitmap(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, si
         if (count) *count = 0;
         return SIEVE_OK;
     }
-    return sieve_bitmap_into(ctx, lo, hi, out_dev, count);
+    return bitmap_into(ctx, lo, hi, out_dev, count);
 }
 
 static int list_impl(sieve_ctx *ctx, uint64_t lo, uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64) {
@@ -607,9 +629,9 @@ static int list_impl(sieve_ctx *ctx, uint64_t lo, uint64_t hi, void *out_dev, si
     }
     rc = ensure_bitmap(ctx, bitmap_words_of(lo, hi));
     if (rc) return rc;
-    rc = sieve_bitmap_into(ctx, lo, hi, ctx->d_bitmap, nullptr);
+    rc = bitmap_into(ctx, lo, hi, ctx->d_bitmap, nullptr);
     if (rc) return rc;
-    return compact(ctx, ctx->d_bitmap, lo, hi, out_dev, cap, n, out64);
+    return compact_with(ctx, ctx->stream, ctx->cs, ctx->d_bitmap, lo, hi, out_dev, cap, n, out64);
 }
 
 int sieve_list(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, size_t cap, uint64_t *n) {
@@ -628,9 +650,7 @@ int sieve_compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo, uint6
     if (hi > (1ull << 32)) return fail(ctx, SIEVE_ERANGE, "uint32 list needs hi <= 2^32");
     if (bitmap_words_of(lo, hi) && !bitmap_dev) return fail(ctx, SIEVE_EINVAL, "null bitmap");
     if ((rc = set_device(ctx))) return rc;
-    rc = ensure_ranges(ctx, 1);
-    if (rc) return rc;
-    return compact(ctx, bitmap_dev, lo, hi, out_dev, cap, n, 0);
+    return compact_with(ctx, ctx->stream, ctx->cs, bitmap_dev, lo, hi, out_dev, cap, n, 0);
 }
 
 int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t m, uint64_t *counts,
@@ -644,60 +664,68 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, si
     }
     int rc = set_device(ctx);
     if (rc) return rc;
-    rc = ensure_ranges(ctx, m);
+    rc = ensure_launch(ctx, m);
     if (rc) return rc;
     const int mode = bitmaps_dev ? kModeBitmap : kModeCount;
-    for (size_t i = 0; i < m; ++i) {
-        uint32_t *bm = bitmaps_dev ? bitmaps_dev[i] : nullptr;
-        ctx->h_ranges[i] = plan_range(ctx->h_primes, lo[i], hi[i], ctx->seg_bytes, mode, bm);
-    }
-    rc = run_sieve_sync(ctx, mode, m);
+    for (size_t i = 0; i < m; ++i)
+        ctx->lb.h_ranges()[i] = plan_range(ctx->h_primes, lo[i], hi[i], ctx->params.seg_bytes, mode,
+                                           bitmaps_dev ? bitmaps_dev[i] : nullptr);
+    bool used = false;
+    rc = batch_graph(ctx, mode, m, &used);
     if (rc) return rc;
-    for (size_t i = 0; i < m; ++i) counts[i] = ctx->h_acc[i];
+    if (!used) {
+        rc = run_sync(ctx, mode, m);
+        if (rc) return rc;
+    }
+    for (size_t i = 0; i < m; ++i) counts[i] = ctx->lb.h_acc[i];
     return SIEVE_OK;
 }
 
 int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
     if (!ctx) return SIEVE_EINVAL;
+    Params &p = ctx->params;
     switch (param) {
         case SIEVE_PARAM_SEGMENT_BYTES:
             if (v < 1024 || v > (int64_t)kMaxSegmentBytes || v % 32) return fail(ctx, SIEVE_EINVAL, "segment bytes");
-            ctx->seg_bytes = (uint32_t)v;
-            return SIEVE_OK;
+            p.seg_bytes = (uint32_t)v;
+            break;
         case SIEVE_PARAM_THREADS:
             if (v != 256 && v != 512 && v != 1024) return fail(ctx, SIEVE_EINVAL, "threads");
-            ctx->threads = (int)v;
-            return SIEVE_OK;
+            p.threads = (int)v;
+            break;
         case SIEVE_PARAM_SMALL_LIMIT:
             if (v < 23 || v > 65536) return fail(ctx, SIEVE_EINVAL, "small limit");
-            ctx->small_limit = (uint32_t)v;
-            return SIEVE_OK;
+            p.small_limit = (uint32_t)v;
+            break;
         case SIEVE_PARAM_CTAS_PER_SM:
             if (v < 1 || v > 8) return fail(ctx, SIEVE_EINVAL, "ctas per sm");
-            ctx->ctas_per_sm = (int)v;
-            return SIEVE_OK;
+            p.ctas_per_sm = (int)v;
+            break;
         case SIEVE_PARAM_CHUNK_SEGMENTS:
             if (v < 1 || v > (int64_t)kMaxChunkSegments) return fail(ctx, SIEVE_EINVAL, "chunk segments");
-            ctx->chunk_segs = (uint32_t)v;
-            return SIEVE_OK;
+            p.chunk_segs = (uint32_t)v;
+            break;
         case SIEVE_PARAM_BUCKET_LIMIT:
             if (v < 0) return fail(ctx, SIEVE_EINVAL, "bucket limit");
-            ctx->bucket_limit = (uint64_t)v;
-            return SIEVE_OK;
+            p.bucket_limit = (uint64_t)v;
+            break;
         default:
             return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
+    drop_graphs(ctx);  // captured launches bake in the launch shape
+    return SIEVE_OK;
 }
 
 int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
     if (!ctx || !v) return SIEVE_EINVAL;
+    const Params &p = ctx->params;
     switch (param) {
-        case SIEVE_PARAM_SEGMENT_BYTES: *v = ctx->seg_bytes; return SIEVE_OK;
-        case SIEVE_PARAM_THREADS: *v = ctx->threads; return SIEVE_OK;
-        case SIEVE_PARAM_SMALL_LIMIT: *v = ctx->small_limit; return SIEVE_OK;
-        case SIEVE_PARAM_CTAS_PER_SM: *v = ctx->ctas_per_sm; return SIEVE_OK;
-        case SIEVE_PARAM_CHUNK_SEGMENTS: *v = ctx->chunk_segs; return SIEVE_OK;
-        case SIEVE_PARAM_BUCKET_LIMIT: *v = (int64_t)ctx->bucket_limit; return SIEVE_OK;
+        case SIEVE_PARAM_SEGMENT_BYTES: *v = p.seg_bytes; return SIEVE_OK;
+        case SIEVE_PARAM_THREADS: *v = p.threads; return SIEVE_OK;
+        case SIEVE_PARAM_SMALL_LIMIT: *v = p.small_limit; return SIEVE_OK;
+        case SIEVE_PARAM_CTAS_PER_SM: *v = p.ctas_per_sm; return SIEVE_OK;
+        case SIEVE_PARAM_CHUNK_SEGMENTS: *v = p.chunk_segs; return SIEVE_OK;
+        case SIEVE_PARAM_BUCKET_LIMIT: *v = (int64_t)p.bucket_limit; return SIEVE_OK;
         default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
 }
@@ -706,7 +734,7 @@ int sieve_get_info(sieve_ctx *ctx, sieve_info *info) {
     if (!ctx || !info) return SIEVE_EINVAL;
     info->hi_max = ctx->hi_max;
     info->prime_limit = ctx->prime_limit;
-    info->n_base_primes = ctx->n_primes;
+    info->n_base_primes = ctx->h_primes.size();
     info->device = ctx->device;
     info->num_sms = ctx->num_sms;
     info->device_bytes = ctx->device_bytes;
@@ -726,9 +754,8 @@ int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clea
     if (rc) return rc;
     // For each base prime p >= 23: #{ m : m >= p, gcd(m, 30) = 1, lo <= p m < hi }.
     auto coprime30_below = [](uint64_t x) -> uint64_t {  // #{ 1 <= m < x : gcd(m, 30) = 1 }
-        static const uint8_t cum[31] = {0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 4, 4, 4,
-                                        4, 5, 5, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 8};
-        if (x == 0) return 0;
+        static const uint8_t cum[30] = {0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 4,
+                                        4, 4, 4, 5, 5, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7};
         return (x / 30) * 8 + cum[x % 30];
     };
     uint64_t total = 0;

@@ -286,8 +286,10 @@ __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v, int lane) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(1024, 1) k_sieve(SieveLaunch P) {
+__global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict__ Pg) {
     extern __shared__ uint4 smem4[];
+    __shared__ SieveLaunch P;  // launch parameters, read from device memory (graph-replayable)
+    if (threadIdx.x == 0) P = *Pg;
     uint8_t *seg = reinterpret_cast<uint8_t *>(smem4);
     uint32_t *seg32 = reinterpret_cast<uint32_t *>(smem4);
     __shared__ WheelTables tab;
@@ -749,13 +751,12 @@ cudaError_t set_sieve_smem_limits() {
     return cudaFuncSetAttribute(k_sieve<kModeBitmap>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_sieve(int mode, const SieveLaunch &L, cudaStream_t stream) {
-    if (L.n_items == 0) return cudaSuccess;
-    const size_t smem = L.seg_bytes;
+cudaError_t launch_sieve(int mode, const SieveLaunch *d_launch, int grid, int threads, uint32_t seg_bytes,
+                         cudaStream_t stream) {
     if (mode == kModeCount)
-        k_sieve<kModeCount><<<L.grid, L.threads, smem, stream>>>(L);
+        k_sieve<kModeCount><<<grid, threads, seg_bytes, stream>>>(d_launch);
     else
-        k_sieve<kModeBitmap><<<L.grid, L.threads, smem, stream>>>(L);
+        k_sieve<kModeBitmap><<<grid, threads, seg_bytes, stream>>>(d_launch);
     return cudaGetLastError();
 }
 

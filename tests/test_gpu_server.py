@@ -1,0 +1,106 @@
+"""The request server (continuous batching): every result is the same alone and
+in the mix (exact), short requests are not held behind long ones, and
+admission and errors behave as declared.  Marked gpu."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only hosts
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1205_4883_gb300 as gb  # noqa: E402
+from paper_1205_4883_gb300.workloads import served_stream  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sv():
+    s = gb.Sieve(10**12 + 2 * 10**9)
+    yield s
+    s.close()
+
+
+def test_mixed_stream_equals_alone(sv):
+    reqs = served_stream(rate=1000.0, n=120, seed=1205, w_exp=(4, 8))
+    with gb.Server(sv, tick_segments=300) as srv:
+        tickets = []
+        for r in reqs:
+            kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
+            rc, t = srv.submit(r.lo, r.hi, kind)
+            assert rc == gb.SIEVE_OK
+            tickets.append(t)
+        results = []
+        for t in tickets:
+            rc, res = srv.poll(t, timeout_us=60_000_000)
+            assert rc == gb.SIEVE_OK and res["status"] == gb.SIEVE_OK
+            results.append(res)
+            assert srv.release(t) == gb.SIEVE_OK
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["in_flight"] == 0
+    for r, res in zip(reqs, results):
+        alone = sv.count(r.lo, r.hi)
+        assert res["count"] == alone, (r.lo, r.hi)
+        if r.kind == "list":
+            lst = sv.primes(r.lo, r.hi, dtype64=True).cpu().numpy().view(np.uint64)
+            assert np.array_equal(res["primes"], lst)
+    # a seeded subset against the oracle
+    for r, res in list(zip(reqs, results))[:25]:
+        assert res["count"] == oracle.count(r.lo, r.hi)
+        if r.kind == "list":
+            assert np.array_equal(res["primes"], oracle.primes(r.lo, r.hi))
+
+
+def test_short_requests_overtake_a_long_one(sv):
+    # a long request advances a few segments per tick; short ones that arrive
+    # meanwhile join the next tick and finish long before it
+    with gb.Server(sv, tick_segments=152) as srv:
+        rc, long_t = srv.submit(0, 10**12)
+        assert rc == gb.SIEVE_OK
+        time.sleep(0.01)
+        shorts = []
+        for k in range(8):
+            lo = 10**11 + k * 10**7
+            rc, t = srv.submit(lo, lo + 10**6, gb.SIEVE_REQ_LIST if k % 2 else gb.SIEVE_REQ_COUNT)
+            assert rc == gb.SIEVE_OK
+            shorts.append((lo, t))
+        for lo, t in shorts:
+            rc, res = srv.poll(t, timeout_us=30_000_000)
+            assert rc == gb.SIEVE_OK
+            assert res["count"] == oracle.count(lo, lo + 10**6)
+            # the long request is still running when the short ones are done
+            rc_long, _ = srv.poll(long_t, timeout_us=0)
+            assert rc_long == gb.SIEVE_ETIMEOUT
+        rc, res = srv.poll(long_t, timeout_us=120_000_000)
+        assert rc == gb.SIEVE_OK and res["count"] == 37607912018
+
+
+def test_admission_and_errors(sv):
+    with gb.Server(sv, max_requests=4, max_device_bytes=64 << 20) as srv:
+        tickets = [srv.submit(10**12, 10**12 + 10**9)[1] for _ in range(4)]
+        rc, _ = srv.submit(0, 100)
+        assert rc == gb.SIEVE_EBUSY  # no free slot
+        with pytest.raises(gb.SieveError) as e:
+            gb.sieve_server_submit(srv.srv, 5, 4)
+        assert e.value.code == gb.SIEVE_EINVAL
+        for t in tickets:
+            assert srv.poll(t, timeout_us=60_000_000)[0] == gb.SIEVE_OK
+            assert srv.release(t) == gb.SIEVE_OK
+        assert srv.release(tickets[0]) == gb.SIEVE_ENOENT
+        # a list request whose bitmap + bound exceed the memory budget is refused
+        rc, _ = srv.submit(0, 10**9, gb.SIEVE_REQ_LIST)
+        assert rc == gb.SIEVE_EBUSY
+        st = srv.stats()
+        assert st["rejected"] == 2 and st["device_bytes_reserved"] == 0
+        # empty ranges complete at once
+        rc, t = srv.submit(7, 7, gb.SIEVE_REQ_LIST)
+        rc, res = srv.poll(t, timeout_us=1_000_000)
+        assert rc == gb.SIEVE_OK and res["count"] == 0
+    with pytest.raises(gb.SieveError) as e:
+        with gb.Server(sv) as srv2:
+            gb.sieve_server_poll(srv2.srv, 12345, 0)
+    assert e.value.code == gb.SIEVE_ENOENT
