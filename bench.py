@@ -166,7 +166,8 @@ def run_gpu(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
-    lo, hi = rank * UNITS, (rank + 1) * UNITS
+    from paper_1205_4883_gb300.workloads import rank_block
+    lo, hi = rank_block(rank, UNITS)
     if args.hi is not None:  # a smaller slice of the workload (profiling)
         lo, hi = rank * UNITS + args.lo, rank * UNITS + args.hi
     units = hi - lo
@@ -260,6 +261,151 @@ def run_gpu(args):
     return line
 
 
+def _event_ms(fn, reps):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_batched(args):
+    """4096 intervals from seed 1205, lo log-uniform in [10^6, 10^14], width log-uniform in
+    [10^3, 10^8]: one graph-replayed persistent launch per step; compared with sieving the
+    same intervals one call at a time and with the plain single-range rate."""
+    import torch
+    import paper_1205_4883_gb300 as gb
+    from paper_1205_4883_gb300.workloads import batch_intervals
+    torch.cuda.set_device(0)
+    los, his = batch_intervals(4096, seed=1205)
+    units = sum(h - l for l, h in zip(los, his))
+    sv = gb.Sieve(max(max(his), 10**14 + 10**10))
+    ref = sv.batch_count(los, his)
+    for _ in range(args.warmup):
+        sv.batch_count(los, his)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        got = sv.batch_count(los, his)
+    dt = (time.perf_counter() - t0) / args.steps
+    assert got == ref
+    t0 = time.perf_counter()
+    for lo, hi in zip(los, his):
+        sv.count(lo, hi)
+    one_by_one = time.perf_counter() - t0
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    plain_ms = _event_ms(lambda: sv.count_dev(10**14, 10**14 + 10**10, out), 3)
+    line = {"metric": METRIC, "value": units / dt, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batched: 4096 intervals, seed 1205, lo log-uniform [1e6, 1e14], "
+                                   "w log-uniform [1e3, 1e8], counts, one graph replay per step",
+                       "integers": units},
+            "one_call_per_interval": {"value": units / one_by_one, "unit": METRIC},
+            "plain_single_range": {"value": 10**10 / (plain_ms * 1e-3), "unit": METRIC,
+                                   "range": "[1e14, 1e14 + 1e10)"}}
+    sv.close()
+    print(json.dumps(line))
+    return 0
+
+
+def run_served(args):
+    """A seeded Poisson stream (80% count, 20% list; lo log-uniform in [0, 1e12], width
+    log-uniform in [1e4, 1e9]) at each offered rate: p50/p99 latency and integers/s."""
+    import numpy as np
+    import torch
+    import paper_1205_4883_gb300 as gb
+    from paper_1205_4883_gb300.workloads import served_stream
+    torch.cuda.set_device(0)
+    sv = gb.Sieve(10**12 + 10**9 + 1)
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    plain_ms = _event_ms(lambda: sv.count_dev(0, 10**11, out), 2)
+    rates = [float(r) for r in args.rates.split(",")]
+    results = []
+    for rate in rates:
+        n = args.requests or int(min(10000, max(300, rate)))
+        reqs = served_stream(rate=rate, n=n, seed=1205)
+        with gb.Server(sv, max_device_bytes=16 << 30) as srv:
+            import queue
+            import threading
+            tickets = queue.Queue()
+            lat = []
+            errors = []
+
+            def collect():  # picks up finished results in any order and releases them (frees slots)
+                outstanding, closed = [], False
+                deadline = time.perf_counter() + 900
+                while (not closed or outstanding) and time.perf_counter() < deadline:
+                    while True:
+                        try:
+                            t = tickets.get_nowait()
+                        except queue.Empty:
+                            break
+                        if t is None:
+                            closed = True
+                        else:
+                            outstanding.append(t)
+                    still = []
+                    for t in outstanding:
+                        rc, res = srv.poll(t, timeout_us=0, copy_primes=False)
+                        if rc == gb.SIEVE_ETIMEOUT:
+                            still.append(t)
+                            continue
+                        if res["status"] != gb.SIEVE_OK:
+                            errors.append(res)
+                        else:
+                            lat.append(res["latency_us"])
+                        srv.release(t)
+                    if len(still) == len(outstanding):
+                        time.sleep(0.0002)
+                    outstanding = still
+                if outstanding:
+                    errors.append(f"{len(outstanding)} requests unfinished after 900 s")
+
+            th = threading.Thread(target=collect)
+            th.start()
+            t0 = time.perf_counter()
+            rejected = 0
+            for r in reqs:
+                now = time.perf_counter() - t0
+                if r.arrival_s > now:
+                    time.sleep(r.arrival_s - now)
+                kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
+                rc, t = srv.submit(r.lo, r.hi, kind)
+                give_up = time.perf_counter() + 120
+                while rc == gb.SIEVE_EBUSY:  # admission is full: retry (bounded)
+                    if time.perf_counter() > give_up:
+                        tickets.put(None)
+                        th.join()
+                        raise RuntimeError("served: a request was refused for 120 s")
+                    rejected += 1
+                    time.sleep(0.0005)
+                    rc, t = srv.submit(r.lo, r.hi, kind)
+                tickets.put(t)
+            tickets.put(None)
+            th.join()
+            wall = time.perf_counter() - t0
+            if errors:
+                raise RuntimeError(f"served requests failed: {errors[:3]}")
+        ints = sum(r.hi - r.lo for r in reqs)
+        results.append({"offered_req_s": rate, "requests": len(reqs), "integers_per_s": ints / wall,
+                        "p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                        "wall_s": wall, "busy_retries": rejected})
+    best = max(r["integers_per_s"] for r in results)
+    line = {"metric": METRIC, "value": best, "unit": METRIC, "n_gpus": 1, "steps": len(rates), "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "served: seeded Poisson stream, 80% count / 20% list, lo log-uniform "
+                                   "[0, 1e12], w log-uniform [1e4, 1e9]", "requests_per_rate": args.requests},
+            "rates": results,
+            "plain_single_range": {"value": 10**11 / (plain_ms * 1e-3), "unit": METRIC, "range": "[0, 1e11)"}}
+    sv.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -269,11 +415,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lo", type=int, default=0, help="with --hi: sieve [lo, hi) of each rank's block instead")
     ap.add_argument("--hi", type=int, default=None)
+    ap.add_argument("--workload", default="pi1e12", choices=["pi1e12", "batched", "served"],
+                    help="pi1e12 (default, the headline line), batched or served")
+    ap.add_argument("--rates", default="100,300,1000,3000,10000", help="served: offered loads, req/s")
+    ap.add_argument("--requests", type=int, default=0,
+                    help="served: requests per rate (0: 1 s of arrivals, between 300 and 10000)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     line = run_gpu(args)
     ws, rank, _ = _dist()
     if rank == 0 and line is not None:

@@ -300,9 +300,10 @@ def sieve_server_submit(srv: int, lo: int, hi: int, kind: int = SIEVE_REQ_COUNT)
     return rc, t.value
 
 
-def sieve_server_poll(srv: int, ticket: int, timeout_us: int = -1):
+def sieve_server_poll(srv: int, ticket: int, timeout_us: int = -1, copy_primes: bool = True):
     """Returns (rc, result dict or None); rc SIEVE_OK or SIEVE_ETIMEOUT (others raise).
-    A list result's primes are copied out of the server's memory."""
+    A list result's primes are copied out of the server's memory (unless copy_primes
+    is False, when only the count is returned)."""
     res = sieve_result()
     rc = load_library().sieve_server_poll(srv, ticket, ctypes.byref(res), timeout_us)
     _check(0, rc, allow=(SIEVE_ETIMEOUT,))
@@ -310,7 +311,7 @@ def sieve_server_poll(srv: int, ticket: int, timeout_us: int = -1):
         return rc, None
     out = {"status": res.status, "kind": res.kind, "count": int(res.count), "latency_us": res.latency_us,
            "primes": None}
-    if res.kind == SIEVE_REQ_LIST and res.status == SIEVE_OK:
+    if copy_primes and res.kind == SIEVE_REQ_LIST and res.status == SIEVE_OK:
         import numpy as np
         n = int(res.count)
         out["primes"] = (np.ctypeslib.as_array(res.primes, shape=(n,)).copy() if n
@@ -344,8 +345,8 @@ class Server:
     def submit(self, lo, hi, kind=SIEVE_REQ_COUNT):
         return sieve_server_submit(self.srv, lo, hi, kind)
 
-    def poll(self, ticket, timeout_us=-1):
-        return sieve_server_poll(self.srv, ticket, timeout_us)
+    def poll(self, ticket, timeout_us=-1, copy_primes=True):
+        return sieve_server_poll(self.srv, ticket, timeout_us, copy_primes)
 
     def release(self, ticket):
         return sieve_server_release(self.srv, ticket)
@@ -430,6 +431,37 @@ class Sieve:
 
     def batch_count(self, lo, hi, bitmaps=None):
         return sieve_batch_count(self.ctx, lo, hi, bitmaps)
+
+    _PARAM_IDS = {"segment_bytes": SIEVE_PARAM_SEGMENT_BYTES, "threads": SIEVE_PARAM_THREADS,
+                  "small_limit": SIEVE_PARAM_SMALL_LIMIT, "ctas_per_sm": SIEVE_PARAM_CTAS_PER_SM,
+                  "chunk_segments": SIEVE_PARAM_CHUNK_SEGMENTS, "bucket_limit": SIEVE_PARAM_BUCKET_LIMIT}
+
+    def apply_plan(self, plan: dict) -> None:
+        """Set the launch parameters of an autotuned plan (see autotune.py)."""
+        for k, v in plan.items():
+            if k in self._PARAM_IDS:
+                sieve_set_param(self.ctx, self._PARAM_IDS[k], int(v))
+
+    def batch_count_tuned(self, lo, hi, table=None):
+        """Counts of many ranges, grouped by autotuner size class; one launch per
+        class with that class's parameters."""
+        from . import autotune
+        table = table if table is not None else autotune.load_table()
+        groups = {}
+        for i, (a, b) in enumerate(zip(lo, hi)):
+            groups.setdefault(autotune.class_key(a, b), []).append(i)
+        out = [0] * len(lo)
+        saved = {k: sieve_get_param(self.ctx, pid) for k, pid in self._PARAM_IDS.items()}
+        try:
+            for key, idx in groups.items():
+                self.apply_plan(saved)
+                self.apply_plan(table.get("classes", {}).get(key, {}))
+                counts = sieve_batch_count(self.ctx, [lo[i] for i in idx], [hi[i] for i in idx])
+                for i, c in zip(idx, counts):
+                    out[i] = c
+        finally:
+            self.apply_plan(saved)
+        return out
 
     def set_param(self, param, value):
         sieve_set_param(self.ctx, param, value)

@@ -42,9 +42,6 @@ constexpr uint32_t kWheelGaps = 0x26424246u;
 // The residues 1, 7, 11, 13, 17, 19, 23, 29 in 5-bit fields.
 constexpr uint64_t kRes40 = 1ull | 7ull << 5 | 11ull << 10 | 13ull << 15 | 17ull << 20 | 19ull << 25 | 23ull << 30 |
                             29ull << 35;
-// #{k : r_k <= x} for x = 0..29 in 4-bit fields (x < 16 in the low word, x >= 16 in the high word).
-constexpr uint64_t kCntLo = 0x4443322221111110ull;
-constexpr uint64_t kCntHi = 0x0087777776666554ull;
 
 __device__ __forceinline__ int wheel_index(uint32_t r) {
     int k = -1;
@@ -205,8 +202,8 @@ struct WheelCursor {
     uint32_t k;
 };
 
-__device__ __forceinline__ WheelCursor wheel_start_any(const WheelTables &t, uint32_t p, uint64_t M, uint32_t pq,
-                                                       uint32_t pc, int64_t B0) {
+__device__ __forceinline__ WheelCursor wheel_start(const WheelTables &t, uint32_t p, uint64_t M, uint32_t pq,
+                                                   uint32_t pc, int64_t B0) {
     const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
     uint64_t Q = __umul64hi(Bc, M);
     uint32_t R = (uint32_t)(Bc - Q * p);
@@ -214,9 +211,10 @@ __device__ __forceinline__ WheelCursor wheel_start_any(const WheelTables &t, uin
         R -= p;
         ++Q;
     }
-    uint32_t k = 0;  // first class with c_k >= R
+    const uint64_t adj = t.adj40[pc];
+    uint32_t k = 0;  // first class with c_k >= R (c_k ascends in k)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) k += (pq * c_res[j] + t.adj[pc * 8 + j]) < R;
+    for (int j = 0; j < 8; ++j) k += (pq * c_res[j] + (uint32_t)((adj >> (5 * j)) & 31u)) < R;
     uint64_t a = Q;
     if (k == 8) {
         k = 0;
@@ -226,49 +224,11 @@ __device__ __forceinline__ WheelCursor wheel_start_any(const WheelTables &t, uin
         a = pq;
         k = pc;
     }
-    uint32_t c_k = 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        if ((uint32_t)j == k) c_k = pq * c_res[j] + t.adj[pc * 8 + j];
+    const uint32_t c_k = pq * (uint32_t)((kRes40 >> (5 * k)) & 31u) + (uint32_t)((adj >> (5 * k)) & 31u);
     WheelCursor w;
     w.off = (int64_t)((uint64_t)p * a + c_k) - B0;
     w.k = k;
     return w;
-}
-
-// wheel_start for a segment that cannot begin before p^2 (see is_early): the
-// first multiple at or after B0 is p Q + c_k with R = B0 mod p and k the first
-// class with c_k >= R.  Since c_k = floor(p r_k / 30), c_k >= R exactly when
-// p r_k >= 30 R, so k = #{r_k < 30 R / p}: estimated in single precision, then
-// corrected with the exact integer test (the estimate is off by at most one
-// class).  Offsets are then 32-bit: c_k - R, or p + c_0 - R past class 7.
-__device__ __forceinline__ WheelCursor wheel_start_late(uint64_t adj, uint32_t p, uint64_t M, uint32_t pq,
-                                                        uint64_t Bc) {
-    const uint32_t R = mod_barrett(Bc, p, M);
-    const uint64_t x30 = 30ull * R;
-    float tf = (float)x30 * __frcp_rn((float)p);
-    uint32_t x = tf < 29.0f ? (uint32_t)tf : 29u;
-    uint32_t k = (uint32_t)((x < 16 ? kCntLo >> (4 * x) : kCntHi >> (4 * (x - 16))) & 15u);
-    if (k < 8 && (uint64_t)p * ((kRes40 >> (5 * k)) & 31u) < x30)
-        ++k;
-    else if (k > 0 && (uint64_t)p * ((kRes40 >> (5 * (k - 1))) & 31u) >= x30)
-        --k;
-    WheelCursor w;
-    if (k == 8) {
-        w.off = (int64_t)(p + pq - R);  // class 0 of the next block: p + c_0 - R, c_0 = pq
-        w.k = 0;
-    } else {
-        w.off = (int64_t)(pq * (uint32_t)((kRes40 >> (5 * k)) & 31u) + (uint32_t)((adj >> (5 * k)) & 31u) - R);
-        w.k = k;
-    }
-    return w;
-}
-
-__device__ __forceinline__ WheelCursor wheel_start(const WheelTables &t, uint32_t p, uint64_t M, uint32_t pq,
-                                                   uint32_t pc, int64_t B0) {
-    const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
-    if (is_early(B0, Bc, p)) return wheel_start_any(t, p, M, pq, pc, B0);
-    return wheel_start_late(t.adj40[pc], p, M, pq, Bc);
 }
 
 // Byte distance from multiple (a, k) to the next one: pq gap_k + dadj_k.

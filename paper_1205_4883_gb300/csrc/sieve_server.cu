@@ -10,8 +10,10 @@
 // Two ticks alternate between two sets of buffers, so the next tick is
 // already queued while the current one runs.  When a tick's event has fired,
 // its counts are added to their requests; a request whose last run is done is
-// completed (list requests are compacted into the host result first).  Host
-// waits poll events and condition variables; no kernel waits on anything.
+// completed; a finished list request is handed to a second host thread that
+// compacts its bitmap on its own stream and copies the primes out through a
+// pinned bounce buffer, so the scheduler keeps launching ticks meanwhile.
+// Host waits poll events and condition variables; no kernel waits on anything.
 
 #include <algorithm>
 #include <chrono>
@@ -45,7 +47,7 @@ struct Req {
     uint64_t *d_list = nullptr;
     uint64_t list_cap = 0;
     size_t arena_off = 0, arena_bytes = 0;
-    std::vector<uint64_t> primes;   // list result
+    std::unique_ptr<uint64_t[]> primes;  // list result (count entries)
     int status = SIEVE_OK;
     bool done = false;
     Clock::time_point t_submit;
@@ -116,7 +118,12 @@ struct sieve_server {
     Arena arena;
 
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_finish;
+    std::deque<Req *> to_finish;       // list requests whose sieving is done
+    bool finisher_stop = false;
+    std::thread finisher;
+    uint64_t *h_bounce = nullptr;      // pinned, kBounceWords
+
     std::map<uint64_t, std::unique_ptr<Req>> reqs;
     std::deque<Req *> active;  // admitted, segments left to schedule or in flight
     uint64_t next_ticket = 1;
@@ -157,50 +164,72 @@ void complete(sieve_server *srv, Req *r, int status) {
     srv->st.in_flight--;
 }
 
-// Called without the lock: compaction of a finished list request.
+constexpr size_t kBounceWords = 8u << 20;  // 64 MiB of uint64
+
+// Called without the lock: compaction of a finished list request into its
+// device list, then a chunked copy to host memory through the pinned buffer.
 int finish_list(sieve_server *srv, Req *r) {
     uint64_t n = 0;
     int rc = compact_with(srv->view, srv->cstream, srv->view->cs, r->d_bitmap, r->lo, r->hi, r->d_list, r->list_cap,
                           &n, 1);
     if (rc) return rc;
-    r->primes.resize(n);
-    if (n) {
-        cudaError_t e = cudaMemcpyAsync(r->primes.data(), r->d_list, n * sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                                        srv->cstream);
+    r->primes.reset(new (std::nothrow) uint64_t[n ? n : 1]);
+    if (!r->primes) return SIEVE_ENOMEM;
+    for (uint64_t done = 0; done < n; done += kBounceWords) {
+        const uint64_t k = std::min<uint64_t>(kBounceWords, n - done);
+        cudaError_t e = cudaMemcpyAsync(srv->h_bounce, r->d_list + done, k * sizeof(uint64_t),
+                                        cudaMemcpyDeviceToHost, srv->cstream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(srv->cstream);
         if (e != cudaSuccess) return cuda_fail(srv->view, e, "list copy");
+        std::memcpy(r->primes.get() + done, srv->h_bounce, k * sizeof(uint64_t));
     }
+    r->count = n;
     return SIEVE_OK;
 }
 
-// Fold a finished tick into its requests (lock held on entry; released around
-// the compaction of finished list requests).
-void harvest(sieve_server *srv, Tick &t, std::unique_lock<std::mutex> &lk) {
-    std::vector<Req *> finished;
+// Fold a finished tick into its requests (lock held).
+void harvest(sieve_server *srv, Tick &t) {
+    bool any = false;
     for (int mode = 0; mode < 2; ++mode) {
         for (size_t i = 0; i < t.runs[mode].size(); ++i) {
             const Run &run = t.runs[mode][i];
-            run.req->count += t.lb[mode].h_acc[i];
-            run.req->done_segs += run.seg_b - run.seg_a;
-            if (run.req->done_segs == run.req->plan.nseg) finished.push_back(run.req);
+            Req *r = run.req;
+            r->count += t.lb[mode].h_acc[i];
+            r->done_segs += run.seg_b - run.seg_a;
+            if (r->done_segs != r->plan.nseg) continue;
+            srv->active.erase(std::remove(srv->active.begin(), srv->active.end(), r), srv->active.end());
+            if (r->kind == SIEVE_REQ_LIST) {
+                srv->to_finish.push_back(r);
+                srv->cv_finish.notify_one();
+            } else {
+                complete(srv, r, SIEVE_OK);
+                any = true;
+            }
         }
         t.runs[mode].clear();
     }
     t.busy = false;
     srv->st.ticks++;
-    for (Req *r : finished) {
-        srv->active.erase(std::remove(srv->active.begin(), srv->active.end(), r), srv->active.end());
-        int rc = SIEVE_OK;
-        if (r->kind == SIEVE_REQ_LIST) {
-            lk.unlock();
-            rc = finish_list(srv, r);
-            lk.lock();
-            srv->arena.release(r->arena_off, r->arena_bytes);
-            srv->st.device_bytes_reserved = srv->arena.used;
-        }
+    if (any) srv->cv_done.notify_all();
+}
+
+// Second host thread: completes list requests (compaction and copy-out).
+void finisher(sieve_server *srv) {
+    cudaSetDevice(srv->view->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    for (;;) {
+        srv->cv_finish.wait(lk, [&] { return srv->finisher_stop || !srv->to_finish.empty(); });
+        if (srv->to_finish.empty()) break;  // stop requested and nothing left
+        Req *r = srv->to_finish.front();
+        srv->to_finish.pop_front();
+        lk.unlock();
+        const int rc = finish_list(srv, r);
+        lk.lock();
+        srv->arena.release(r->arena_off, r->arena_bytes);
+        srv->st.device_bytes_reserved = srv->arena.used;
         complete(srv, r, rc);
+        srv->cv_done.notify_all();
     }
-    if (!finished.empty()) srv->cv_done.notify_all();
 }
 
 // Take runs from the active requests and launch them on tick t (lock held).
@@ -262,7 +291,7 @@ void scheduler(sieve_server *srv) {
             if (!t.busy) continue;
             cudaError_t q = cudaEventQuery(t.ev);
             if (q == cudaSuccess) {
-                harvest(srv, t, lk);
+                harvest(srv, t);
             } else if (q != cudaErrorNotReady) {
                 t.busy = false;
                 fail_all(srv, cuda_fail(srv->view, q, "tick"));
@@ -346,7 +375,10 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server arena"));
     srv->arena.size = srv->cfg.max_device_bytes;
     srv->arena.free_blocks[0] = srv->arena.size;
+    e = cudaMallocHost(&srv->h_bounce, kBounceWords * sizeof(uint64_t));
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server bounce buffer"));
     srv->th = std::thread(scheduler, srv.get());
+    srv->finisher = std::thread(finisher, srv.get());
     *out = srv.release();
     return SIEVE_OK;
 }
@@ -413,8 +445,8 @@ int sieve_server_poll(sieve_server *srv, uint64_t ticket, sieve_result *res, int
     }
     res->status = r->status;
     res->kind = r->kind;
-    res->count = r->kind == SIEVE_REQ_LIST ? (uint64_t)r->primes.size() : r->count;
-    res->primes = r->kind == SIEVE_REQ_LIST ? r->primes.data() : nullptr;
+    res->count = r->count;
+    res->primes = (r->kind == SIEVE_REQ_LIST && r->status == SIEVE_OK) ? r->primes.get() : nullptr;
     res->latency_us = r->latency_us;
     return SIEVE_OK;
 }
@@ -444,6 +476,12 @@ void sieve_server_destroy(sieve_server *srv) {
     }
     srv->cv_work.notify_all();
     if (srv->th.joinable()) srv->th.join();
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->finisher_stop = true;
+    }
+    srv->cv_finish.notify_all();
+    if (srv->finisher.joinable()) srv->finisher.join();
     if (srv->view) {
         cudaSetDevice(srv->view->device);
         if (srv->stream) cudaStreamSynchronize(srv->stream);
@@ -455,6 +493,7 @@ void sieve_server_destroy(sieve_server *srv) {
         sieve_destroy(srv->view);
     }
     if (srv->arena.base) cudaFree(srv->arena.base);
+    if (srv->h_bounce) cudaFreeHost(srv->h_bounce);
     if (srv->stream) cudaStreamDestroy(srv->stream);
     if (srv->cstream) cudaStreamDestroy(srv->cstream);
     delete srv;

@@ -100,6 +100,13 @@ def served_stream(rate: float, n: int, seed: int = 1205, list_frac: float = 0.2,
     return out
 
 
+def rank_block(rank: int, units: int = PI_1E12[1]) -> Tuple[int, int]:
+    """The block of integers rank `rank` sieves when several GPUs run the
+    single-range workload side by side: [rank units, (rank + 1) units)
+    (independent ranges, no exchange between ranks; weak scaling)."""
+    return rank * units, (rank + 1) * units
+
+
 def random_ranges(count: int, seed: int, max_lo: int, max_w: int) -> List[Tuple[int, int]]:
     """`count` ranges [lo, lo + w) with lo uniform in [0, max_lo] and w uniform in [0, max_w]."""
     rng = SplitMix64(seed)

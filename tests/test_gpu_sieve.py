@@ -251,3 +251,14 @@ def test_batch_with_bitmaps(sv):
         if bms[i] is not None:
             nw = gb.sieve_bitmap_words(a, b)
             assert np.array_equal(bms[i][:nw].cpu().numpy().view(np.uint32), oracle.bitmap(a, b)), i
+
+
+def test_batch_tuned_equals_untuned(sv):
+    from paper_1205_4883_gb300 import autotune
+    los, his = batch_intervals(300, seed=3, lo_exp=(2, 13), w_exp=(1, 7))
+    table = {"classes": {"0/0": {"segment_bytes": 32768, "small_limit": 256},
+                         "1/1": {"segment_bytes": 65536, "threads": 512},
+                         "2/2": {"bucket_limit": 0, "chunk_segments": 4}}}
+    assert sv.batch_count_tuned(los, his, table) == sv.batch_count(los, his)
+    assert sv.get_param(gb.SIEVE_PARAM_SEGMENT_BYTES) == 229376  # restored
+    assert autotune.class_key(los[0], his[0]) in {f"{a}/{b}" for a in range(3) for b in range(4)}
