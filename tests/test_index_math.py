@@ -22,7 +22,7 @@ def inv_mod128(p):
 def test_128_subprogressions_cover_the_progression_with_fixed_banks():
     # warp-cooperative small primes: lane l, q in 0..3 takes bytes = 4 l + q (mod 128)
     rng = random.Random(1)
-    for _ in range(1500):
+    for _ in range(400):
         p = rng.choice([23, 29, 31, 37, 41, 101, 997, 1787, 1789])
         L = rng.choice([32, 64, 1024, 4128, 229376])
         off = rng.randrange(0, L)
@@ -43,8 +43,9 @@ def test_128_subprogressions_cover_the_progression_with_fixed_banks():
 def test_four_phase_subprogressions_cover_the_progression():
     # medium primes: p^-1 = p (mod 4), so off + ((ph - off) p mod 4) p = ph (mod 4)
     rng = random.Random(2)
-    for _ in range(5000):
-        p = rng.choice(small_primes(40000)[300:])
+    mediums = small_primes(40000)[300:]
+    for _ in range(1500):
+        p = rng.choice(mediums)
         L = rng.choice([32, 1024, 4128, 229376])
         off = rng.randrange(0, L)
         got = []
@@ -95,10 +96,10 @@ def _direct(p, B0, span):
 
 def test_wheel_cursor_walk_equals_the_definition():
     rng = random.Random(3)
-    primes = small_primes(200000)
-    for _ in range(2500):
+    primes = small_primes(60000)
+    for _ in range(400):
         p = rng.choice(primes)
-        span = rng.choice([64, 1024, 229376, 4 * 229376])
+        span = rng.choice([64, 1024, 8192, 65536])
         B0 = rng.choice([-32, -2, 0, 1, rng.randrange(0, 10**6), p * p // 30 - rng.randrange(0, 3 * p),
                          rng.randrange(0, p * p // 30 + 5 * p + 1)])
         B0 = max(B0, -32)
