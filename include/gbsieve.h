@@ -240,6 +240,9 @@ void sieve_server_destroy(sieve_server *srv);
 #define SIEVE_PARAM_CHUNK_SEGMENTS 5 /* consecutive segments per work item (1..64) */
 #define SIEVE_PARAM_BUCKET_LIMIT  6 /* primes >= this go through bucket lists; 0 = segment bytes;
                                        default 2^62 (off: direct crossing measured faster) */
+#define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
+                                       primes, carried across the segments of a work item; used
+                                       when they fit (default 64; 0 = recompute per segment) */
 
 /* Set a launch parameter for later calls on ctx (SIEVE_EINVAL if out of range). */
 int sieve_set_param(sieve_ctx *ctx, int param, int64_t value);

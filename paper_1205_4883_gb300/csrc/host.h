@@ -20,6 +20,7 @@ struct Params {
     int ctas_per_sm = 1;
     uint32_t chunk_segs = 16;
     uint64_t bucket_limit = 1ull << 62;  // primes >= this use the bucket lists; 0: the segment size
+    uint32_t cursor_mb = 64;             // budget for per-CTA large-prime cursors (0: recompute every segment)
 };
 
 // Everything one sieve launch reads and writes besides the resident state:
@@ -50,6 +51,11 @@ struct BucketStore {
     double slack = 1.15;  // capacity = slack x expected hits + 4096, raised on overflow
 };
 
+struct CursorStore {
+    uint32_t *d = nullptr;
+    size_t entries = 0;
+};
+
 struct GraphKey {
     size_t m;
     int mode;
@@ -78,6 +84,7 @@ struct sieve_ctx {
     gbs::LaunchBuffers lb;
     gbs::CompactScratch cs;
     gbs::BucketStore buckets;
+    gbs::CursorStore cursors;
     uint32_t *d_bitmap = nullptr;  // list scratch
     size_t bitmap_cap = 0;         // words
 
@@ -107,7 +114,7 @@ void free_compact_scratch(sieve_ctx *ctx, CompactScratch &cs);
 // `stream`: fills in the launch header, copies the block, clears the
 // accumulators and launches.  Bucket lists are used only if `bs` is given.
 int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
-                  BucketStore *bs);
+                  BucketStore *bs, CursorStore *cs = nullptr);
 
 // Compact the odd-only bitmap of [lo, hi) into out_dev (uint32 or uint64).
 // *n = primes in the range (2 included); SIEVE_ETRUNC if cap < *n.

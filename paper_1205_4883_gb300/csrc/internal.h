@@ -63,6 +63,8 @@ struct SieveLaunch {
     uint32_t *buckets;                   // grid x chunk_segs x bucket_cap entries
     uint32_t bucket_cap;                 // entries per segment list
     unsigned *overflow;                  // set to 1 if a list overflowed (zeroed before the launch)
+    uint32_t *cursors;                   // null, or grid x cursor_stride wheel cursors of the large primes
+    uint32_t cursor_stride;              // large primes per CTA (from mid_end)
     const uint8_t *tile;                 // kTileCopies shifted copies of the pattern
     uint64_t tile_stride;                // bytes between copies
     uint32_t seg_bytes;                  // S, multiple of 32, <= kMaxSegmentBytes

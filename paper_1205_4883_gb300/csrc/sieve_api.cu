@@ -191,7 +191,7 @@ RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t 
 }
 
 int prepare_launch(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t m, BucketStore *bs,
-                   uint64_t *items_out) {
+                   CursorStore *cs, uint64_t *items_out) {
     const std::vector<uint32_t> &h = ctx->h_primes;
     RangeDesc *rd = lb.h_ranges();
     uint64_t segs = 0;
@@ -207,10 +207,15 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t 
     const uint64_t blim = prm.bucket_limit ? prm.bucket_limit : prm.seg_bytes;
     const uint32_t bfirst = std::max(first_at_least(h, blim), mid_end);
     const bool buckets = bs && bfirst < nmax;
-    // Chunks (several segments per work item) only pay off with bucket lists;
-    // keep at least 4 items per CTA so the last wave stays short.
+    // Per-CTA cursors for the large primes (4 B each) when they fit the budget
+    // and every offset fits 29 bits (p < 2^27); not with bucket lists.
+    const uint32_t n_large = nmax > mid_end ? nmax - mid_end : 0;
+    const bool cursors = cs && !buckets && n_large && h[nmax - 1] < (1u << 27) &&
+                         (uint64_t)grid * n_large * 4 <= (uint64_t)prm.cursor_mb << 20;
+    // Chunks (several segments per work item) pay off with bucket lists and
+    // cursors; keep at least 4 items per CTA so the last wave stays short.
     uint32_t C = 1;
-    if (buckets) {
+    if (buckets || cursors) {
         C = prm.chunk_segs;
         while (C > 1 && segs / C < 4 * grid) C /= 2;
     }
@@ -255,6 +260,18 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t 
         L.buckets = bs->d;
         L.bucket_cap = (uint32_t)cap;
     }
+    if (cursors && C > 1) {
+        const size_t need = (size_t)grid * n_large;
+        if (need > cs->entries) {
+            dev_free(ctx, cs->d, cs->entries);
+            cs->entries = 0;
+            int rc = dev_alloc(ctx, &cs->d, need);
+            if (rc) return rc;
+            cs->entries = need;
+        }
+        L.cursors = cs->d;
+        L.cursor_stride = n_large;
+    }
     *items_out = items;
     return SIEVE_OK;
 }
@@ -271,9 +288,9 @@ int enqueue_launch(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int m
 }
 
 int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
-                  BucketStore *bs) {
+                  BucketStore *bs, CursorStore *cs) {
     uint64_t items = 0;
-    int rc = prepare_launch(ctx, prm, lb, m, bs, &items);
+    int rc = prepare_launch(ctx, prm, lb, m, bs, cs, &items);
     if (rc) return rc;
     const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
     return enqueue_launch(ctx, stream, prm, mode, lb, m, (int)std::min<uint64_t>(grid, items));
@@ -324,7 +341,7 @@ int finish(sieve_ctx *ctx, LaunchBuffers &lb, size_t m, int *overflowed) {
 // hit counts).  Counts are left in ctx->lb.h_acc[0..m).
 int run_sync(sieve_ctx *ctx, int mode, size_t m) {
     for (int attempt = 0; attempt < 4; ++attempt) {
-        int rc = launch_ranges(ctx, ctx->stream, ctx->params, mode, ctx->lb, m, &ctx->buckets);
+        int rc = launch_ranges(ctx, ctx->stream, ctx->params, mode, ctx->lb, m, &ctx->buckets, &ctx->cursors);
         if (rc) return rc;
         int of = 0;
         rc = finish(ctx, ctx->lb, m, &of);
@@ -459,7 +476,7 @@ int batch_graph(sieve_ctx *ctx, int mode, size_t m, bool *used) {
     *used = false;
     const Params &prm = ctx->params;
     uint64_t items = 0;
-    int rc = prepare_launch(ctx, prm, ctx->lb, m, nullptr, &items);
+    int rc = prepare_launch(ctx, prm, ctx->lb, m, nullptr, &ctx->cursors, &items);
     if (rc) return rc;
     {
         const uint64_t blim = prm.bucket_limit ? prm.bucket_limit : prm.seg_bytes;
@@ -562,6 +579,7 @@ void sieve_destroy(sieve_ctx *ctx) {
     }
     cudaFree(ctx->d_bitmap);
     cudaFree(ctx->buckets.d);
+    cudaFree(ctx->cursors.d);
     free_launch_buffers(ctx, ctx->lb);
     free_compact_scratch(ctx, ctx->cs);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
@@ -595,7 +613,7 @@ int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_de
     rc = ensure_launch(ctx, 1);
     if (rc) return rc;
     ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeCount, nullptr);
-    rc = launch_ranges(ctx, ctx->stream, ctx->params, kModeCount, ctx->lb, 1, &ctx->buckets);
+    rc = launch_ranges(ctx, ctx->stream, ctx->params, kModeCount, ctx->lb, 1, &ctx->buckets, &ctx->cursors);
     if (rc) return rc;
     // the count, or UINT64_MAX if a bucket list overflowed
     CK(launch_finalize_count(ctx->lb.d_acc + 1, reinterpret_cast<const unsigned *>(ctx->lb.d_acc + 2), count_dev,
@@ -709,6 +727,10 @@ int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
             if (v < 0) return fail(ctx, SIEVE_EINVAL, "bucket limit");
             p.bucket_limit = (uint64_t)v;
             break;
+        case SIEVE_PARAM_CURSOR_MB:
+            if (v < 0 || v > 4096) return fail(ctx, SIEVE_EINVAL, "cursor budget");
+            p.cursor_mb = (uint32_t)v;
+            break;
         default:
             return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
@@ -726,6 +748,7 @@ int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
         case SIEVE_PARAM_CTAS_PER_SM: *v = p.ctas_per_sm; return SIEVE_OK;
         case SIEVE_PARAM_CHUNK_SEGMENTS: *v = p.chunk_segs; return SIEVE_OK;
         case SIEVE_PARAM_BUCKET_LIMIT: *v = (int64_t)p.bucket_limit; return SIEVE_OK;
+        case SIEVE_PARAM_CURSOR_MB: *v = p.cursor_mb; return SIEVE_OK;
         default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
 }

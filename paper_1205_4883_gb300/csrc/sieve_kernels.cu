@@ -348,6 +348,10 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             __syncthreads();
         }
 
+        // per-CTA wheel cursors of the large primes, carried from segment to
+        // segment of this chunk; valid for primes [mid_end, n_prev)
+        uint32_t *const cursors = P.cursors ? P.cursors + (size_t)blockIdx.x * P.cursor_stride : nullptr;
+        uint32_t n_prev = 0;
         for (uint32_t g = 0; g < nchunk; ++g) {
             const uint64_t s = s0 + g;
             const int64_t B0 = Bs + (int64_t)g * S;
@@ -424,19 +428,30 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             }
             // 2a'. large primes below the bucket limit [mid_end, n_use): one lane
             //      per prime, walking its multiples in the segment with the wheel
-            //      cursor (only the hits are visited, not all eight classes)
+            //      cursor (only the hits are visited, not all eight classes).  With
+            //      per-CTA cursors the walk resumes where the previous segment of
+            //      this chunk left it, so only primes new to the chunk pay for the
+            //      start computation (Barrett reduction and wheel class).
             for (uint32_t base = mid_end + (tid & ~31u); base < n_use; base += blockDim.x) {
                 const uint32_t i = base + lane;
                 const bool valid = i < n_use;
                 const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
-                const uint64_t M = valid ? __ldg(P.magic + i) : ~0ull;
                 const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
-                const WheelCursor wc = wheel_start(tab, p, M, pq, pc, B0);
-                uint32_t off = (valid && wc.off < (int64_t)L) ? (uint32_t)wc.off : L;
-                uint32_t k = wc.k;
+                uint32_t off, k;
+                if (cursors && i < n_prev) {  // (offset from this segment's start) | class << 29
+                    const uint32_t st = cursors[i - mid_end];
+                    off = st & 0x1fffffffu;
+                    k = st >> 29;
+                } else {
+                    const WheelCursor wc = wheel_start(tab, p, valid ? __ldg(P.magic + i) : ~0ull, pq, pc, B0);
+                    off = (valid && wc.off < (int64_t)0x7fffffff) ? (uint32_t)wc.off : 0x7fffffffu;
+                    k = wc.k;
+                }
                 const uint32_t bits = tab.bits24[pc], dadj = tab.dadj24[pc];
-                for (; off < L; off += wheel_step(pq, dadj, k), k = (k + 1) & 7u)
+                const uint32_t l = valid ? L : 0u;
+                for (; off < l; off += wheel_step(pq, dadj, k), k = (k + 1) & 7u)
                     clear_bit(seg32, off, (bits >> (3 * k)) & 7u);
+                if (cursors && valid) cursors[i - mid_end] = (off - L) | (k << 29);
                 __syncwarp();
             }
             // 2c. drain this segment's bucket list
@@ -554,6 +569,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                     atomicAdd(P.counts + range_id, v);
                 }
             }
+            n_prev = n_use;
             __syncthreads();
         }
     }

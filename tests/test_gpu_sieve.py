@@ -262,3 +262,22 @@ def test_batch_tuned_equals_untuned(sv):
     assert sv.batch_count_tuned(los, his, table) == sv.batch_count(los, his)
     assert sv.get_param(gb.SIEVE_PARAM_SEGMENT_BYTES) == 229376  # restored
     assert autotune.class_key(los[0], his[0]) in {f"{a}/{b}" for a in range(3) for b in range(4)}
+
+
+@pytest.mark.parametrize("lo,hi", [(0, 10**10), (99 * 10**10, 10**12), (10**9 - 5, 10**9 + 4 * 10**9),
+                                   (4 * 10**12, 4 * 10**12 + 10**10)])
+def test_large_prime_cursors_match_recomputation(lo, hi):
+    # chunks of consecutive segments carry the large primes' wheel cursors; primes
+    # whose p^2 enters mid-chunk start fresh.  Same results as recomputing per segment.
+    with gb.Sieve(5 * 10**12) as s:
+        s.set_param(gb.SIEVE_PARAM_CHUNK_SEGMENTS, 64)
+        with_cursors = s.count(lo, hi)
+        wa, _ = s.bitmap(lo, min(hi, lo + 2 * 10**9))
+        s.set_param(gb.SIEVE_PARAM_CURSOR_MB, 0)
+        assert s.count(lo, hi) == with_cursors
+        wb, _ = s.bitmap(lo, min(hi, lo + 2 * 10**9))
+        assert torch.equal(wa, wb)
+    if (lo, hi) == (0, 10**10):
+        assert with_cursors == PI[10**10]
+    else:
+        assert with_cursors == oracle.count(lo, hi)
