@@ -26,6 +26,10 @@ sys.path.insert(0, ROOT)
 
 UNITS = 10**12                     # integers per rank per step
 METRIC = "integers sieved/s"
+# DRAM bytes (read + write) of one k_sieve<0> launch on this workload, from
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass, full launch);
+# reported only while the kernel source is the one it was measured on.
+TRAFFIC = {"kernel_sha256_16": "279205550de1b6d4", "bytes": 10.85e6 + 7.41e6}
 WORKLOAD = "pi(10^12): count primes in [0, 10^12), one range, count-only, mod-30 wheel + pattern of 7..19"
 
 
@@ -34,6 +38,16 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def _traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_1205_4883_gb300", "csrc", "sieve_kernels.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return TRAFFIC["bytes"] if sha == TRAFFIC["kernel_sha256_16"] else None
 
 
 def _peaks():
@@ -246,7 +260,8 @@ def run_gpu(args):
                        "parallelism": f"{ws} independent ranges" if ws > 1 else "1 range"},
             "roofline": {"bound": "alu", "op": "shared-memory bit-clear (atom.shared.and)",
                          "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
-                         "frac": achieved / peak_ops, "traffic": None,
+                         "frac": achieved / peak_ops,
+                         "traffic": _traffic() if args.hi is None and ws == 1 else None,
                          "peak_basis": f"{n_sms} SMs x 32 lanes/clk x {sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
                          "work_per_launch": clears},
             "clocks": clocks,

@@ -240,6 +240,11 @@ void sieve_server_destroy(sieve_server *srv);
 #define SIEVE_PARAM_CHUNK_SEGMENTS 5 /* consecutive segments per work item (1..64) */
 #define SIEVE_PARAM_BUCKET_LIMIT  6 /* primes >= this go through bucket lists; 0 = segment bytes;
                                        default 2^62 (off: direct crossing measured faster) */
+#define SIEVE_PARAM_MR_PERCENT    8 /* a range of width w < this % of the base primes above 2^16
+                                       it would need is sieved with the primes below 2^16 only and
+                                       its survivors tested by deterministic Miller-Rabin (the first
+                                       twelve primes as bases, exact for n < 3.18e23); 0 = never;
+                                       default 0 (off: measured slower) */
 #define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
                                        primes, carried across the segments of a work item; used
                                        when they fit (default 64; 0 = recompute per segment) */

@@ -21,6 +21,7 @@ struct Params {
     uint32_t chunk_segs = 16;
     uint64_t bucket_limit = 1ull << 62;  // primes >= this use the bucket lists; 0: the segment size
     uint32_t cursor_mb = 64;             // budget for per-CTA large-prime cursors (0: recompute every segment)
+    uint32_t mr_percent = 0;             // Miller-Rabin path when width < this % of the skipped primes (0: off)
 };
 
 // Everything one sieve launch reads and writes besides the resident state:
@@ -34,6 +35,16 @@ struct LaunchBuffers {
     size_t cap = 0;                        // ranges
     RangeDesc *h_ranges() const { return reinterpret_cast<RangeDesc *>(h_block + kLaunchHeader); }
     RangeDesc *d_ranges() const { return reinterpret_cast<RangeDesc *>(d_block + kLaunchHeader); }
+    // after the ranges: the indices of the ranges on the Miller-Rabin path
+    uint32_t *h_mr() const { return reinterpret_cast<uint32_t *>(h_block + kLaunchHeader + cap * sizeof(RangeDesc)); }
+    uint32_t *d_mr() const { return reinterpret_cast<uint32_t *>(d_block + kLaunchHeader + cap * sizeof(RangeDesc)); }
+    static size_t block_bytes(size_t cap) { return kLaunchHeader + cap * (sizeof(RangeDesc) + sizeof(uint32_t)); }
+};
+
+// Words the Miller-Rabin path needs for ranges without an output bitmap.
+struct MrScratch {
+    uint32_t *d = nullptr;
+    size_t words = 0;
 };
 
 // Scratch of the bitmap -> list compaction.
@@ -85,6 +96,7 @@ struct sieve_ctx {
     gbs::CompactScratch cs;
     gbs::BucketStore buckets;
     gbs::CursorStore cursors;
+    gbs::MrScratch mr;
     uint32_t *d_bitmap = nullptr;  // list scratch
     size_t bitmap_cap = 0;         // words
 

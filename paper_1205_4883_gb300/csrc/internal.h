@@ -42,7 +42,7 @@ struct RangeDesc {
     uint64_t bitmap_words;  // words of the odd-only bitmap of [lo, hi)
     uint64_t corr;          // primes the wheel cannot hold (2, 3, 5) in range
     uint32_t n_use;         // base primes with p * p < hi (prefix length)
-    uint32_t pad;
+    uint32_t mr;            // 1: sieve with the primes below 2^16, then Miller-Rabin (one segment)
 };
 static_assert(sizeof(RangeDesc) == 72, "RangeDesc layout");
 
@@ -63,6 +63,10 @@ struct SieveLaunch {
     uint32_t *buckets;                   // grid x chunk_segs x bucket_cap entries
     uint32_t bucket_cap;                 // entries per segment list
     unsigned *overflow;                  // set to 1 if a list overflowed (zeroed before the launch)
+    uint32_t mr_end;                     // index of the first base prime >= 2^16
+    uint64_t mr_square;                  // that prime squared: survivors below it need no test
+    const uint32_t *mr_list;             // ranges on the Miller-Rabin path
+    uint32_t n_mr;
     uint32_t *cursors;                   // null, or grid x cursor_stride wheel cursors of the large primes
     uint32_t cursor_stride;              // large primes per CTA (from mid_end)
     const uint8_t *tile;                 // kTileCopies shifted copies of the pattern
@@ -84,6 +88,8 @@ cudaError_t launch_magic(const uint32_t *primes, uint64_t *magic, uint64_t n, cu
 cudaError_t launch_sieve(int mode, const SieveLaunch *d_launch, int grid, int threads, uint32_t seg_bytes,
                          cudaStream_t stream);
 cudaError_t set_sieve_smem_limits();
+// Miller-Rabin test of the survivors of the ranges in d_launch->mr_list.
+cudaError_t launch_mr_filter(int mode, const SieveLaunch *d_launch, int grid, cudaStream_t stream);
 
 // Compaction of an odd-only bitmap into a prime list.
 constexpr uint32_t kCompactTileWords = 2048;  // 256 threads x 8 words

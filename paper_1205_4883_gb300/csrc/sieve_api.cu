@@ -115,7 +115,7 @@ int alloc_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb, size_t m) {
     if (m <= lb.cap) return SIEVE_OK;
     free_launch_buffers(ctx, lb);
     const size_t cap = std::max<size_t>(m, 64);
-    const size_t block = kLaunchHeader + cap * sizeof(RangeDesc);
+    const size_t block = LaunchBuffers::block_bytes(cap);
     int rc = dev_alloc(ctx, &lb.d_block, block);
     if (rc) return rc;
     rc = dev_alloc(ctx, &lb.d_acc, cap + 2);
@@ -127,7 +127,7 @@ int alloc_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb, size_t m) {
 }
 
 void free_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb) {
-    const size_t block = kLaunchHeader + lb.cap * sizeof(RangeDesc);
+    const size_t block = LaunchBuffers::block_bytes(lb.cap);
     if (lb.d_block) dev_free(ctx, lb.d_block, block);
     if (lb.d_acc) dev_free(ctx, lb.d_acc, lb.cap + 2);
     if (lb.h_block) cudaFreeHost(lb.h_block);
@@ -190,7 +190,7 @@ RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t 
     return r;
 }
 
-int prepare_launch(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t m, BucketStore *bs,
+int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &lb, size_t m, BucketStore *bs,
                    CursorStore *cs, uint64_t *items_out) {
     const std::vector<uint32_t> &h = ctx->h_primes;
     RangeDesc *rd = lb.h_ranges();
@@ -224,6 +224,46 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t 
         rd[i].item_first = items;
         items += (rd[i].nseg + C - 1) / C;
     }
+    // Miller-Rabin path for narrow ranges high up: sieving with the primes below
+    // 2^16 and testing the survivors (about 5 % of the integers, each some 10^4
+    // instructions when prime) beats visiting every base prime (about 100
+    // instructions each) when the width is below mr_percent % of the primes
+    // that would be skipped.
+    // Such a range is one segment long; a count-mode one keeps its raw wheel
+    // words (and a bitmap-mode one without an output its odd-only words) in
+    // scratch for k_mr_filter.
+    const uint32_t mr_end = first_at_least(h, 65536);
+    const uint64_t mr_square = mr_end < h.size() ? (uint64_t)h[mr_end] * h[mr_end] : ~0ull;
+    uint32_t n_mr = 0;
+    size_t scratch_words = 0;
+    std::vector<size_t> scratch_at;
+    for (size_t i = 0; i < m; ++i) {
+        rd[i].mr = 0;
+        if (prm.mr_percent && rd[i].nseg == 1 && rd[i].n_use > mr_end && rd[i].hi > mr_square &&
+            (rd[i].hi - rd[i].lo) * 100 < (uint64_t)prm.mr_percent * (rd[i].n_use - mr_end)) {
+            rd[i].mr = 1;
+            lb.h_mr()[n_mr++] = (uint32_t)i;
+            if (mode == kModeCount) {  // raw wheel words of the one segment
+                const int64_t need = (((int64_t)rd[i].hi - 30 * rd[i].Bbase + 29) / 30 + 31) & ~31ll;
+                scratch_at.push_back(scratch_words);
+                scratch_words += (size_t)need / 4;
+            } else if (!rd[i].bitmap) {
+                scratch_at.push_back(scratch_words);
+                scratch_words += rd[i].bitmap_words;
+            } else {
+                scratch_at.push_back(~(size_t)0);
+            }
+        }
+    }
+    if (scratch_words > ctx->mr.words) {
+        dev_free(ctx, ctx->mr.d, ctx->mr.words);
+        ctx->mr.words = 0;
+        int rc = dev_alloc(ctx, &ctx->mr.d, std::max<size_t>(scratch_words, 1 << 16));
+        if (rc) return rc;
+        ctx->mr.words = std::max<size_t>(scratch_words, 1 << 16);
+    }
+    for (uint32_t q = 0; q < n_mr; ++q)
+        if (scratch_at[q] != ~(size_t)0) rd[lb.h_mr()[q]].bitmap = ctx->mr.d + scratch_at[q];
     SieveLaunch &L = *reinterpret_cast<SieveLaunch *>(lb.h_block);
     std::memset(&L, 0, sizeof L);
     L.ranges = lb.d_ranges();
@@ -240,6 +280,10 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t 
     L.chunk_segs = C;
     L.small_end = small_end;
     L.mid_end = mid_end;
+    L.mr_end = mr_end;
+    L.mr_square = mr_square;
+    L.mr_list = lb.d_mr();
+    L.n_mr = n_mr;
     L.bucket_first = 0xffffffffu;
     if (buckets) {
         // expected hits per full segment: 8 S / p per bucket prime (one per wheel
@@ -276,24 +320,29 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t 
     return SIEVE_OK;
 }
 
+// grid: sieve CTAs (0: no sieve launch); mr_grid: Miller-Rabin CTAs (0: none);
+// n_list: entries of the Miller-Rabin list to copy.
 int enqueue_launch(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
-                   int grid) {
-    const size_t block = kLaunchHeader + m * sizeof(RangeDesc);
-    CK(cudaMemcpyAsync(lb.d_block, lb.h_block, block, cudaMemcpyHostToDevice, stream));
+                   int grid, int mr_grid, size_t n_list) {
+    CK(cudaMemcpyAsync(lb.d_block, lb.h_block, kLaunchHeader + m * sizeof(RangeDesc), cudaMemcpyHostToDevice, stream));
+    if (n_list)
+        CK(cudaMemcpyAsync(lb.d_mr(), lb.h_mr(), n_list * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
     CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
-    if (grid > 0)
-        CK(launch_sieve(mode, reinterpret_cast<const SieveLaunch *>(lb.d_block), grid, prm.threads, prm.seg_bytes,
-                        stream));
+    const SieveLaunch *d = reinterpret_cast<const SieveLaunch *>(lb.d_block);
+    if (grid > 0) CK(launch_sieve(mode, d, grid, prm.threads, prm.seg_bytes, stream));
+    if (mr_grid > 0) CK(launch_mr_filter(mode, d, mr_grid, stream));
     return SIEVE_OK;
 }
 
 int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
                   BucketStore *bs, CursorStore *cs) {
     uint64_t items = 0;
-    int rc = prepare_launch(ctx, prm, lb, m, bs, cs, &items);
+    int rc = prepare_launch(ctx, prm, mode, lb, m, bs, cs, &items);
     if (rc) return rc;
     const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
-    return enqueue_launch(ctx, stream, prm, mode, lb, m, (int)std::min<uint64_t>(grid, items));
+    const uint32_t n_mr = reinterpret_cast<const SieveLaunch *>(lb.h_block)->n_mr;
+    return enqueue_launch(ctx, stream, prm, mode, lb, m, (int)std::min<uint64_t>(grid, items),
+                          (int)std::min<uint64_t>(n_mr, 4ull * ctx->num_sms), n_mr);
 }
 
 int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
@@ -476,7 +525,7 @@ int batch_graph(sieve_ctx *ctx, int mode, size_t m, bool *used) {
     *used = false;
     const Params &prm = ctx->params;
     uint64_t items = 0;
-    int rc = prepare_launch(ctx, prm, ctx->lb, m, nullptr, &ctx->cursors, &items);
+    int rc = prepare_launch(ctx, prm, mode, ctx->lb, m, nullptr, &ctx->cursors, &items);
     if (rc) return rc;
     {
         const uint64_t blim = prm.bucket_limit ? prm.bucket_limit : prm.seg_bytes;
@@ -492,7 +541,7 @@ int batch_graph(sieve_ctx *ctx, int mode, size_t m, bool *used) {
         const int grid = ctx->num_sms * prm.ctas_per_sm;
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_launch(ctx, ctx->capture_stream, prm, mode, ctx->lb, m, grid);
+        rc = enqueue_launch(ctx, ctx->capture_stream, prm, mode, ctx->lb, m, grid, 4 * ctx->num_sms, m);
         cudaError_t e1 = cudaMemcpyAsync(ctx->lb.h_acc, ctx->lb.d_acc + 1, (m + 1) * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToHost, ctx->capture_stream);
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -580,6 +629,7 @@ void sieve_destroy(sieve_ctx *ctx) {
     cudaFree(ctx->d_bitmap);
     cudaFree(ctx->buckets.d);
     cudaFree(ctx->cursors.d);
+    cudaFree(ctx->mr.d);
     free_launch_buffers(ctx, ctx->lb);
     free_compact_scratch(ctx, ctx->cs);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
@@ -731,6 +781,10 @@ int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
             if (v < 0 || v > 4096) return fail(ctx, SIEVE_EINVAL, "cursor budget");
             p.cursor_mb = (uint32_t)v;
             break;
+        case SIEVE_PARAM_MR_PERCENT:
+            if (v < 0 || v > 1000000) return fail(ctx, SIEVE_EINVAL, "Miller-Rabin percent");
+            p.mr_percent = (uint32_t)v;
+            break;
         default:
             return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
@@ -749,6 +803,7 @@ int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
         case SIEVE_PARAM_CHUNK_SEGMENTS: *v = p.chunk_segs; return SIEVE_OK;
         case SIEVE_PARAM_BUCKET_LIMIT: *v = (int64_t)p.bucket_limit; return SIEVE_OK;
         case SIEVE_PARAM_CURSOR_MB: *v = p.cursor_mb; return SIEVE_OK;
+        case SIEVE_PARAM_MR_PERCENT: *v = p.mr_percent; return SIEVE_OK;
         default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
 }

@@ -39,6 +39,8 @@ struct WheelTables {
 // Gaps between consecutive residues coprime to 30 (1, 7, 11, ..., 29, 31) in
 // 4-bit fields: 6, 4, 2, 4, 2, 4, 6, 2.
 constexpr uint32_t kWheelGaps = 0x26424246u;
+// Large primes a lane handles per pass of the large-prime loop (loads in flight).
+constexpr uint32_t kLargeUnroll = 4;
 // The residues 1, 7, 11, 13, 17, 19, 23, 29 in 5-bit fields.
 constexpr uint64_t kRes40 = 1ull | 7ull << 5 | 11ull << 10 | 13ull << 15 | 17ull << 20 | 19ull << 25 | 23ull << 30 |
                             29ull << 35;
@@ -165,6 +167,58 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
+// ---------------------------------------------------------------- Miller-Rabin
+
+// Montgomery product a b R^-1 mod n (R = 2^64) for odd n < 2^62 and a, b < n,
+// with nprime = -n^-1 mod 2^64: t = a b, m = (t mod R) nprime, and
+// (t + m n) / R < 2 n, less n if needed.  The low word of t + m n is 0, so
+// the carry out of it is 1 exactly when t's low word is not 0.
+__device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t n, uint64_t nprime) {
+    const uint64_t lo = a * b, hi = __umul64hi(a, b);
+    const uint64_t m = lo * nprime;
+    const uint64_t r = hi + __umul64hi(m, n) + (lo != 0);
+    return r >= n ? r - n : r;
+}
+
+// Deterministic Miller-Rabin for odd n < 2^62 with no prime factor below 37:
+// the first twelve primes as bases decide every n < 3.18e23 (Sorenson and
+// Webster, "Strong pseudoprimes to twelve prime bases", Math. Comp. 86, 2017).
+// a^d mod n is the paper's exponentiation by squaring (Section 3.2, Algorithm
+// 2), carried out on Montgomery residues.
+__device__ __noinline__ bool mr_is_prime(uint64_t n) {
+    uint64_t inv = n;  // n^-1 mod 2^64 by Newton steps (n is its own inverse mod 8)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) inv *= 2 - n * inv;
+    const uint64_t nprime = 0 - inv;
+    const uint64_t one = (0 - n) % n;  // R mod n: Montgomery form of 1
+    uint64_t r2 = one;                 // R^2 mod n by 64 doublings
+    for (int i = 0; i < 64; ++i) {
+        r2 <<= 1;
+        if (r2 >= n) r2 -= n;
+    }
+    const uint64_t minus_one = n - one;
+    uint64_t d = n - 1;
+    const int s = __ffsll((long long)d) - 1;
+    d >>= s;
+    const uint32_t bases[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    for (int b = 0; b < 12; ++b) {
+        uint64_t y = mont_mul(bases[b], r2, n, nprime);  // a R mod n
+        uint64_t x = one;
+        for (uint64_t e = d; e; e >>= 1) {  // Algorithm 2: x = a^d mod n
+            if (e & 1) x = mont_mul(x, y, n, nprime);
+            y = mont_mul(y, y, n, nprime);
+        }
+        if (x == one || x == minus_one) continue;
+        bool witness = true;
+        for (int r = 1; r < s && witness; ++r) {
+            x = mont_mul(x, x, n, nprime);
+            if (x == minus_one) witness = false;
+        }
+        if (witness) return false;
+    }
+    return true;
+}
+
 // Number of base primes among primes[0, n) with p^2 < E (a prefix, since the
 // primes ascend), found by one warp with 32-way probing.  Every lane of the
 // warp must call it; all lanes return the result.
@@ -203,7 +257,7 @@ struct WheelCursor {
 };
 
 __device__ __forceinline__ WheelCursor wheel_start(const WheelTables &t, uint32_t p, uint64_t M, uint32_t pq,
-                                                   uint32_t pc, int64_t B0) {
+                                                       uint32_t pc, int64_t B0) {
     const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
     uint64_t Q = __umul64hi(Bc, M);
     uint32_t R = (uint32_t)(Bc - Q * p);
@@ -230,6 +284,7 @@ __device__ __forceinline__ WheelCursor wheel_start(const WheelTables &t, uint32_
     w.k = k;
     return w;
 }
+
 
 // Byte distance from multiple (a, k) to the next one: pq gap_k + dadj_k.
 __device__ __forceinline__ uint32_t wheel_step(uint32_t pq, uint32_t dadj, uint32_t k) {
@@ -386,7 +441,8 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                                          __ldg(P.magic + kFirstCrossingPrime + t));
             }
             __syncthreads();
-            const uint32_t n_seg = s_nseg;
+            // a range on the Miller-Rabin path is sieved with the primes below 2^16 only
+            const uint32_t n_seg = rd.mr && P.mr_end < s_nseg ? P.mr_end : s_nseg;
             // primes crossed here (not through the buckets): [8, n_use)
             const uint32_t n_use = use_buckets && P.bucket_first < n_seg ? P.bucket_first : n_seg;
             const uint32_t small_end = P.small_end < n_use ? P.small_end : n_use;
@@ -432,26 +488,42 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             //      per-CTA cursors the walk resumes where the previous segment of
             //      this chunk left it, so only primes new to the chunk pay for the
             //      start computation (Barrett reduction and wheel class).
-            for (uint32_t base = mid_end + (tid & ~31u); base < n_use; base += blockDim.x) {
-                const uint32_t i = base + lane;
-                const bool valid = i < n_use;
-                const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
-                const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
-                uint32_t off, k;
-                if (cursors && i < n_prev) {  // (offset from this segment's start) | class << 29
-                    const uint32_t st = cursors[i - mid_end];
-                    off = st & 0x1fffffffu;
-                    k = st >> 29;
-                } else {
-                    const WheelCursor wc = wheel_start(tab, p, valid ? __ldg(P.magic + i) : ~0ull, pq, pc, B0);
-                    off = (valid && wc.off < (int64_t)0x7fffffff) ? (uint32_t)wc.off : 0x7fffffffu;
-                    k = wc.k;
+            // Each lane takes kLargeUnroll primes per pass and issues all their
+            // loads first: the loop is bound by load latency, not by arithmetic.
+            for (uint32_t base = mid_end + (tid & ~31u) * kLargeUnroll; base < n_use;
+                 base += blockDim.x * kLargeUnroll) {
+                uint32_t pv[kLargeUnroll], sv[kLargeUnroll];
+                uint64_t mv[kLargeUnroll];
+#pragma unroll
+                for (int u = 0; u < (int)kLargeUnroll; ++u) {
+                    const uint32_t i = base + lane + 32u * u;
+                    const bool valid = i < n_use;
+                    pv[u] = valid ? __ldg(P.primes + i) : 1u;
+                    const bool resume = valid && cursors && i < n_prev;
+                    sv[u] = resume ? cursors[i - mid_end] : 0u;
+                    mv[u] = (valid && !resume) ? __ldg(P.magic + i) : ~0ull;
                 }
-                const uint32_t bits = tab.bits24[pc], dadj = tab.dadj24[pc];
-                const uint32_t l = valid ? L : 0u;
-                for (; off < l; off += wheel_step(pq, dadj, k), k = (k + 1) & 7u)
-                    clear_bit(seg32, off, (bits >> (3 * k)) & 7u);
-                if (cursors && valid) cursors[i - mid_end] = (off - L) | (k << 29);
+#pragma unroll
+                for (int u = 0; u < (int)kLargeUnroll; ++u) {
+                    const uint32_t i = base + lane + 32u * u;
+                    const bool valid = i < n_use;
+                    const uint32_t p = pv[u];
+                    const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
+                    uint32_t off, k;
+                    if (valid && cursors && i < n_prev) {  // (offset from this segment's start) | class << 29
+                        off = sv[u] & 0x1fffffffu;
+                        k = sv[u] >> 29;
+                    } else {
+                        const WheelCursor wc = wheel_start(tab, p, mv[u], pq, pc, B0);
+                        off = (valid && wc.off < (int64_t)0x7fffffff) ? (uint32_t)wc.off : 0x7fffffffu;
+                        k = wc.k;
+                    }
+                    const uint32_t bits = tab.bits24[pc], dadj = tab.dadj24[pc];
+                    const uint32_t l = valid ? L : 0u;
+                    for (; off < l; off += wheel_step(pq, dadj, k), k = (k + 1) & 7u)
+                        clear_bit(seg32, off, (bits >> (3 * k)) & 7u);
+                    if (cursors && valid) cursors[i - mid_end] = (off - L) | (k << 29);
+                }
                 __syncwarp();
             }
             // 2c. drain this segment's bucket list
@@ -503,9 +575,12 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
 
             unsigned long long cnt = 0;
             if (MODE == kModeCount) {
-                // 4. popcount of the bits in [lo, hi)
+                // 4. popcount of the bits in [lo, hi); a range on the Miller-Rabin
+                //    path also leaves its raw wheel words for k_mr_filter
+                uint32_t *const raw = rd.mr ? rd.bitmap : nullptr;
                 for (uint32_t w = tid; w < L / 4; w += blockDim.x) {
                     uint32_t v = seg32[w];
+                    if (raw) raw[w] = v;
                     const int64_t wb = 120 * (int64_t)w;
                     if (wb < lo_rel || wb + 120 > hi_rel) v &= range_mask(wb, lo_rel, hi_rel);
                     cnt += __popc(v);
@@ -572,6 +647,57 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             n_prev = n_use;
             __syncthreads();
         }
+    }
+}
+
+// ---------------------------------------------------------------- Miller-Rabin filter
+
+// Survivors of the sieve by the primes below 2^16 in the ranges on the
+// Miller-Rabin path (P->mr_list[0 .. P->n_mr)), one CTA per range: every
+// survivor in [lo, hi) at or above P->mr_square is tested; a composite is
+// subtracted from its range's count and, in bitmap mode, loses its bit.
+// Count mode reads the raw wheel words k_sieve left (ODD = false); bitmap mode
+// the odd-only words of the output (ODD = true).  Each such range is one
+// segment long.
+template <bool ODD>
+__global__ void __launch_bounds__(256) k_mr_filter(const SieveLaunch *__restrict__ P) {
+    __shared__ unsigned long long s_red[8];
+    const uint32_t n_mr = P->n_mr;
+    for (uint32_t q = blockIdx.x; q < n_mr; q += gridDim.x) {
+        const uint32_t r = P->mr_list[q];
+        const RangeDesc &rd = P->ranges[r];
+        uint32_t *words = rd.bitmap;
+        unsigned long long composites = 0;
+        if (words) {
+            const uint64_t o0 = rd.lo | 1;
+            const int64_t base_int = 30 * rd.Bbase;
+            const uint64_t nwords = ODD ? rd.bitmap_words
+                                        : (uint64_t)((((int64_t)rd.hi - base_int + 29) / 30 + 31) & ~31ll) / 4;
+            for (uint64_t w = threadIdx.x; w < nwords; w += blockDim.x) {
+                uint32_t v = words[w], keep = v;
+                while (v) {
+                    const int b = __ffs(v) - 1;
+                    v &= v - 1;
+                    const int64_t n = ODD ? (int64_t)(o0 + 64 * w + 2 * (uint64_t)b)
+                                          : base_int + 120 * (int64_t)w + 30 * (b >> 3) + (int64_t)c_res[b & 7];
+                    if (n < (int64_t)rd.lo || n >= (int64_t)rd.hi || (uint64_t)n < P->mr_square) continue;
+                    if (!mr_is_prime((uint64_t)n)) {
+                        keep &= ~(1u << b);
+                        ++composites;
+                    }
+                }
+                if (ODD && keep != words[w]) words[w] = keep;
+            }
+        }
+        composites = warp_sum(composites);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = composites;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long c = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) c += s_red[i];
+            if (c) atomicAdd(P->counts + r, 0ull - c);
+        }
+        __syncthreads();
     }
 }
 
@@ -733,6 +859,14 @@ cudaError_t launch_sieve(int mode, const SieveLaunch *d_launch, int grid, int th
         k_sieve<kModeCount><<<grid, threads, seg_bytes, stream>>>(d_launch);
     else
         k_sieve<kModeBitmap><<<grid, threads, seg_bytes, stream>>>(d_launch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mr_filter(int mode, const SieveLaunch *d_launch, int grid, cudaStream_t stream) {
+    if (mode == kModeCount)
+        k_mr_filter<false><<<grid, 256, 0, stream>>>(d_launch);
+    else
+        k_mr_filter<true><<<grid, 256, 0, stream>>>(d_launch);
     return cudaGetLastError();
 }
 

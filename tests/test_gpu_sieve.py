@@ -281,3 +281,35 @@ def test_large_prime_cursors_match_recomputation(lo, hi):
         assert with_cursors == PI[10**10]
     else:
         assert with_cursors == oracle.count(lo, hi)
+
+
+@pytest.mark.parametrize("lo,w", [(10**12 + 7, 10**5), (10**13 + 11, 3 * 10**4), (10**14, 10**5),
+                                  (2**32 + 1, 5 * 10**5), (4295098369 - 500, 1000)])
+def test_miller_rabin_path_matches(sv, lo, w):
+    # narrow ranges high up: sieve with the primes below 2^16, then Miller-Rabin
+    hi = lo + w
+    s = sv
+    s.set_param(gb.SIEVE_PARAM_MR_PERCENT, 10**6)  # force the path
+    try:
+        c_mr = s.count(lo, hi)
+        bm_mr, _ = s.bitmap(lo, hi)
+        lst_mr = s.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)
+        counts_mr = s.batch_count([lo, lo + 17, lo + w // 2], [hi, hi - 3, hi])
+    finally:
+        s.set_param(gb.SIEVE_PARAM_MR_PERCENT, 0)
+    assert c_mr == s.count(lo, hi) == oracle.count(lo, hi)
+    bm_sieve, _ = s.bitmap(lo, hi)
+    assert torch.equal(bm_mr, bm_sieve)
+    assert np.array_equal(lst_mr, oracle.primes(lo, hi))
+    assert counts_mr == [oracle.count(lo, hi), oracle.count(lo + 17, hi - 3), oracle.count(lo + w // 2, hi)]
+    s.set_param(gb.SIEVE_PARAM_MR_PERCENT, 0)
+
+
+def test_miller_rabin_path_rejects_strong_pseudoprimes():
+    with gb.Sieve(4 * 10**14) as s:
+        s.set_param(gb.SIEVE_PARAM_MR_PERCENT, 10**6)
+        for n in (2152302898747, 3474749660383, 341550071728321):
+            lo, hi = n - 2000, n + 2000
+            got = [int(v) for v in s.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)]
+            assert n not in got
+            assert got == [x for x in range(lo, hi) if mr_is_prime(x)]

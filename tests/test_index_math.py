@@ -115,3 +115,60 @@ def test_grid_origin_aligns_odd_words():
         t0 = lo - ((lo % 960 - t0_res) % 960)
         assert t0 <= lo < t0 + 960 and t0 % 30 == 0 and (t0 + 1 - o0) % 64 == 0
         assert t0 // 30 >= -32
+
+
+def test_montgomery_miller_rabin_as_the_kernel_does_it():
+    # mont_mul / mr_is_prime of the kernel, 64-bit wraparound written out,
+    # against the Miller-Rabin the oracle tests are pinned with
+    from numtheory import mr_is_prime as reference
+    m64 = (1 << 64) - 1
+
+    def mont_mul(a, b, n, nprime):
+        lo, hi = (a * b) & m64, (a * b) >> 64
+        m = (lo * nprime) & m64
+        r = hi + ((m * n) >> 64) + (1 if lo else 0)
+        return r - n if r >= n else r
+
+    def kernel_mr(n):
+        inv = n
+        for _ in range(5):
+            inv = (inv * (2 - n * inv)) & m64
+        nprime = (-inv) & m64
+        one = ((-n) & m64) % n
+        r2 = one
+        for _ in range(64):
+            r2 <<= 1
+            if r2 >= n:
+                r2 -= n
+        minus_one = n - one
+        d = n - 1
+        s = (d & -d).bit_length() - 1
+        d >>= s
+        for a in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37):
+            y, x, e = mont_mul(a, r2, n, nprime), one, d
+            while e:
+                if e & 1:
+                    x = mont_mul(x, y, n, nprime)
+                y = mont_mul(y, y, n, nprime)
+                e >>= 1
+            if x in (one, minus_one):
+                continue
+            for _ in range(1, s):
+                x = mont_mul(x, x, n, nprime)
+                if x == minus_one:
+                    break
+            else:
+                return False
+        return True
+
+    rng = random.Random(4)
+    small = (3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
+    done = 0
+    while done < 1500:
+        n = rng.randrange(2**32, 2**62) | 1
+        if any(n % p == 0 for p in small):
+            continue
+        assert kernel_mr(n) == reference(n), n
+        done += 1
+    for n in (2152302898747, 3474749660383, 341550071728321):  # strong pseudoprimes to small bases
+        assert not kernel_mr(n)
