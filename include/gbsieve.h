@@ -235,7 +235,7 @@ void sieve_server_destroy(sieve_server *srv);
 /* Tunable launch parameters (see sieve_set_param / sieve_get_param). */
 #define SIEVE_PARAM_SEGMENT_BYTES 1 /* shared-memory segment, bytes; multiple of 32 */
 #define SIEVE_PARAM_THREADS       2 /* threads per CTA: 256, 512 or 1024 */
-#define SIEVE_PARAM_SMALL_LIMIT   3 /* primes below this are crossed warp-cooperatively */
+#define SIEVE_PARAM_SMALL_LIMIT   3 /* primes below this are crossed warp-cooperatively (default 512) */
 #define SIEVE_PARAM_CTAS_PER_SM   4 /* persistent CTAs per SM */
 #define SIEVE_PARAM_CHUNK_SEGMENTS 5 /* consecutive segments per work item (1..64) */
 #define SIEVE_PARAM_BUCKET_LIMIT  6 /* primes >= this go through bucket lists; 0 = segment bytes;
@@ -245,6 +245,9 @@ void sieve_server_destroy(sieve_server *srv);
                                        its survivors tested by deterministic Miller-Rabin (the first
                                        twelve primes as bases, exact for n < 3.18e23); 0 = never;
                                        default 0 (off: measured slower) */
+#define SIEVE_PARAM_MID_LIMIT     9 /* primes from the small limit up to this are crossed one lane
+                                       per prime with per-byte-phase sub-progressions, larger ones
+                                       by walking the wheel; 0 = segment bytes / 8 (default) */
 #define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
                                        primes, carried across the segments of a work item; used
                                        when they fit (default 64; 0 = recompute per segment) */

@@ -34,6 +34,7 @@ SIEVE_PARAM_CHUNK_SEGMENTS = 5
 SIEVE_PARAM_BUCKET_LIMIT = 6
 SIEVE_PARAM_CURSOR_MB = 7
 SIEVE_PARAM_MR_PERCENT = 8
+SIEVE_PARAM_MID_LIMIT = 9
 
 _u64 = ctypes.c_uint64
 _i64 = ctypes.c_int64
@@ -437,7 +438,8 @@ class Sieve:
     _PARAM_IDS = {"segment_bytes": SIEVE_PARAM_SEGMENT_BYTES, "threads": SIEVE_PARAM_THREADS,
                   "small_limit": SIEVE_PARAM_SMALL_LIMIT, "ctas_per_sm": SIEVE_PARAM_CTAS_PER_SM,
                   "chunk_segments": SIEVE_PARAM_CHUNK_SEGMENTS, "bucket_limit": SIEVE_PARAM_BUCKET_LIMIT,
-                  "cursor_mb": SIEVE_PARAM_CURSOR_MB, "mr_percent": SIEVE_PARAM_MR_PERCENT}
+                  "cursor_mb": SIEVE_PARAM_CURSOR_MB, "mr_percent": SIEVE_PARAM_MR_PERCENT,
+                  "mid_limit": SIEVE_PARAM_MID_LIMIT}
 
     def apply_plan(self, plan: dict) -> None:
         """Set the launch parameters of an autotuned plan (see autotune.py)."""

@@ -32,7 +32,7 @@ LO_BANDS = [(0, 10), (10, 13), (13, 19)]
 W_BANDS = [(0, 5), (5, 7), (7, 9), (9, 19)]
 
 PARAM_KEYS = {"segment_bytes": 1, "threads": 2, "small_limit": 3, "ctas_per_sm": 4,
-              "chunk_segments": 5, "bucket_limit": 6}
+              "chunk_segments": 5, "bucket_limit": 6, "cursor_mb": 7, "mid_limit": 9}
 
 
 def band(x: int, bands) -> int:
@@ -73,7 +73,7 @@ def sample_class(lo_band, w_band, n: int, seed: int, hi_max: int) -> Tuple[List[
 
 def candidates(quick: bool):
     segs = [65536, 229376] if quick else [32768, 65536, 131072, 229376]
-    smalls = [1792] if quick else [896, 1792, 3584]
+    smalls = [512] if quick else [256, 512, 896]
     threads = [1024] if quick else [512, 1024]
     buckets = [1 << 62, 0]
     chunks = [16]

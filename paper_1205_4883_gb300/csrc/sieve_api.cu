@@ -203,7 +203,8 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
     const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
     const uint32_t small_end = first_at_least(h, prm.small_limit);
     // primes below S / 8 have at least 8 hits per progression in a full segment
-    const uint32_t mid_end = std::max(small_end, first_at_least(h, std::max<uint32_t>(prm.seg_bytes / 8, 23)));
+    const uint32_t mid_lim = prm.mid_limit ? prm.mid_limit : std::max<uint32_t>(prm.seg_bytes / 8, 23);
+    const uint32_t mid_end = std::max(small_end, first_at_least(h, mid_lim));
     const uint64_t blim = prm.bucket_limit ? prm.bucket_limit : prm.seg_bytes;
     const uint32_t bfirst = std::max(first_at_least(h, blim), mid_end);
     const bool buckets = bs && bfirst < nmax;
@@ -781,6 +782,10 @@ int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
             if (v < 0 || v > 4096) return fail(ctx, SIEVE_EINVAL, "cursor budget");
             p.cursor_mb = (uint32_t)v;
             break;
+        case SIEVE_PARAM_MID_LIMIT:
+            if (v < 0 || v > (1ll << 31)) return fail(ctx, SIEVE_EINVAL, "mid limit");
+            p.mid_limit = (uint32_t)v;
+            break;
         case SIEVE_PARAM_MR_PERCENT:
             if (v < 0 || v > 1000000) return fail(ctx, SIEVE_EINVAL, "Miller-Rabin percent");
             p.mr_percent = (uint32_t)v;
@@ -804,6 +809,7 @@ int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
         case SIEVE_PARAM_BUCKET_LIMIT: *v = (int64_t)p.bucket_limit; return SIEVE_OK;
         case SIEVE_PARAM_CURSOR_MB: *v = p.cursor_mb; return SIEVE_OK;
         case SIEVE_PARAM_MR_PERCENT: *v = p.mr_percent; return SIEVE_OK;
+        case SIEVE_PARAM_MID_LIMIT: *v = p.mid_limit; return SIEVE_OK;
         default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
 }
