@@ -563,8 +563,14 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                     const uint32_t kappa = ((4u * (uint32_t)lane + q - off) * pinv) & 127u;
                     const uint32_t o = off + kappa * p;  // = 4 lane + q (mod 128)
                     const uint32_t mask = ~(1u << (8u * q + bit));
-#pragma unroll 4
-                    for (uint32_t w = o >> 2; w < Lw; w += wstep) atomicAnd(&seg32[w], mask);
+                    uint32_t w = o >> 2;
+                    for (; w + 3u * wstep < Lw; w += 4u * wstep) {
+                        atomicAnd(&seg32[w], mask);
+                        atomicAnd(&seg32[w + wstep], mask);
+                        atomicAnd(&seg32[w + 2u * wstep], mask);
+                        atomicAnd(&seg32[w + 3u * wstep], mask);
+                    }
+                    for (; w < Lw; w += wstep) atomicAnd(&seg32[w], mask);
                 }
             }
             __syncthreads();
