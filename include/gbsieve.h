@@ -248,6 +248,15 @@ void sieve_server_destroy(sieve_server *srv);
 #define SIEVE_PARAM_MID_LIMIT     9 /* primes from the small limit up to this are crossed one lane
                                        per prime with per-byte-phase sub-progressions, larger ones
                                        by walking the wheel; 0 = segment bytes / 8 (default) */
+#define SIEVE_PARAM_WHEEL         10 /* count-only calls (sieve_count, sieve_count_dev,
+                                        sieve_batch_count without bitmaps) sieve on the mod-30 wheel
+                                        (30, default) or the mod-210 wheel (210: 48 bits per 210
+                                        integers, multiples of 7 not crossed); results are the same */
+#define SIEVE_PARAM_SMALL_LIMIT_210 11 /* mod-210 wheel: primes below this are crossed one warp per
+                                          (prime, class) with conflict-free lanes (default 128) */
+#define SIEVE_PARAM_MID_LIMIT_210 12 /* mod-210 wheel: primes from the small limit up to this are
+                                        crossed one lane per prime with per-class sub-progressions,
+                                        larger ones by the wheel walk (0 = segment words / 6) */
 #define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
                                        primes, carried across the segments of a work item; used
                                        when they fit (default 64; 0 = recompute per segment) */
@@ -278,7 +287,8 @@ int sieve_base_primes(sieve_ctx *ctx, uint32_t *out, size_t cap, uint64_t *n);
 /*
  * Exact number of bit-clears the crossing-off loop performs for [lo, hi):
  * the multiples p*m in [lo, hi) with p a base prime >= 23, m >= p and m
- * coprime to 30 (the mod-30 wheel after the pre-sieve of 7..19).  Host-only
+ * coprime to 30 (the mod-30 wheel after the pre-sieve of 7..19), or coprime
+ * to 210 when SIEVE_PARAM_WHEEL is 210 (the count path's wheel).  Host-only
  * arithmetic; this is the algorithmic work used as a roofline numerator.
  */
 int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clears);

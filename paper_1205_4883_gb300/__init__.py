@@ -35,6 +35,9 @@ SIEVE_PARAM_BUCKET_LIMIT = 6
 SIEVE_PARAM_CURSOR_MB = 7
 SIEVE_PARAM_MR_PERCENT = 8
 SIEVE_PARAM_MID_LIMIT = 9
+SIEVE_PARAM_WHEEL = 10
+SIEVE_PARAM_SMALL_LIMIT_210 = 11
+SIEVE_PARAM_MID_LIMIT_210 = 12
 
 _u64 = ctypes.c_uint64
 _i64 = ctypes.c_int64
@@ -439,7 +442,8 @@ class Sieve:
                   "small_limit": SIEVE_PARAM_SMALL_LIMIT, "ctas_per_sm": SIEVE_PARAM_CTAS_PER_SM,
                   "chunk_segments": SIEVE_PARAM_CHUNK_SEGMENTS, "bucket_limit": SIEVE_PARAM_BUCKET_LIMIT,
                   "cursor_mb": SIEVE_PARAM_CURSOR_MB, "mr_percent": SIEVE_PARAM_MR_PERCENT,
-                  "mid_limit": SIEVE_PARAM_MID_LIMIT}
+                  "mid_limit": SIEVE_PARAM_MID_LIMIT, "wheel": SIEVE_PARAM_WHEEL,
+                  "small_limit_210": SIEVE_PARAM_SMALL_LIMIT_210, "mid_limit_210": SIEVE_PARAM_MID_LIMIT_210}
 
     def apply_plan(self, plan: dict) -> None:
         """Set the launch parameters of an autotuned plan (see autotune.py)."""

@@ -23,6 +23,9 @@ struct Params {
     uint64_t bucket_limit = 1ull << 62;  // primes >= this use the bucket lists; 0: the segment size
     uint32_t cursor_mb = 64;             // budget for per-CTA large-prime cursors (0: recompute every segment)
     uint32_t mr_percent = 0;             // Miller-Rabin path when width < this % of the skipped primes (0: off)
+    int wheel = 30;                      // count-only launches on the mod-30 or the mod-210 wheel
+    uint32_t small_limit210 = 128;       // mod-210: primes below this are crossed warp-cooperatively
+    uint32_t mid_limit210 = 0;           // mod-210: primes below this use per-class sub-progressions; 0: words / 6
 };
 
 // Everything one sieve launch reads and writes besides the resident state:
@@ -91,6 +94,10 @@ struct sieve_ctx {
     std::vector<uint32_t> h_primes;
     uint8_t *d_tile = nullptr;
     uint64_t tile_stride = 0;
+    // the same for the mod-210 count path: pattern of 11..19 and the class tables
+    uint8_t *d_tile210 = nullptr;
+    uint64_t tile210_stride = 0;
+    gbs::W210Tables *d_tab210 = nullptr;
 
     gbs::Params params;
     gbs::LaunchBuffers lb;
@@ -126,6 +133,10 @@ void free_compact_scratch(sieve_ctx *ctx, CompactScratch &cs);
 // Sieve the m ranges lb.h_ranges()[0..m) (planned with plan_range) on
 // `stream`: fills in the launch header, copies the block, clears the
 // accumulators and launches.  Bucket lists are used only if `bs` is given.
+RangeDesc plan_range210(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_words);
+uint32_t w210_segment_words(const Params &prm);
+int launch_ranges210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, LaunchBuffers &lb, size_t m,
+                     CursorStore *cs);
 int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
                   BucketStore *bs, CursorStore *cs = nullptr);
 

@@ -91,6 +91,36 @@ cudaError_t set_sieve_smem_limits();
 // Miller-Rabin test of the survivors of the ranges in d_launch->mr_list.
 cudaError_t launch_mr_filter(int mode, const SieveLaunch *d_launch, int grid, cudaStream_t stream);
 
+// Count path on the mod-210 wheel (sieve_w210.cu): 48 bits per group of 210
+// integers, bit 48 g + i <-> 210 g + r_i (r_i the residues coprime to 210,
+// ascending), packed LSB-first into 32-bit words; segments of a multiple of 3
+// words (2 whole groups per 3 words).  The launch block and RangeDesc are
+// shared with the mod-30 kernels: Bbase is the first group (lo / 210), corr
+// counts 2, 3, 5 and 7, and SieveLaunch::seg_bytes is the segment's size in
+// bytes (a multiple of 12).
+constexpr uint32_t kW210Period = 46189u;            // 11 * 13 * 17 * 19 groups
+constexpr uint32_t kW210PeriodBytes = 277134u;      // 6 bytes per group
+constexpr uint32_t kW210MaxSegmentBytes = 229368u;  // 57342 words (a multiple of 3)
+constexpr uint32_t kW210MaxSmemBytes = 229376u;     // the segment rounded up to 16-byte copies
+// Group 0 as it must read after sieving: the residues 1, 121, 143, 169, 187 and
+// 209 (bits 0, 27, 32, 38, 42, 47) are not prime, the other 42 are.
+constexpr uint32_t kW210Group0Lo = 0xf7fffffeu;  // bits 0..31
+constexpr uint32_t kW210Group0Hi = 0x7bbeu;      // bits 32..47
+struct W210Tables {
+    uint16_t step[48 * 48];  // [class of p][k]: bit of class k | dadj_k << 6 | (gap_k / 2) << 10
+    uint8_t adj[48 * 48];    // [class of p][k]: floor(r_pc r_k / 210)
+    uint8_t bit[48 * 48];    // [class of p][k]: index of (r_pc r_k) mod 210
+    uint8_t idx[210];        // residue -> index, 0xff if not coprime to 210
+    uint8_t cnt[210];        // v -> #{ i : r_i <= v }
+    uint8_t r48[48];         // the residues
+};
+void build_w210_tables(W210Tables *t);  // host
+cudaError_t set_sieve210_smem_limit();
+cudaError_t launch_sieve210(const SieveLaunch *d_launch, const W210Tables *tab, const uint8_t *tile,
+                            uint64_t tile_stride, int grid, int threads, uint32_t seg_bytes, cudaStream_t stream);
+cudaError_t launch_build_tile210(const W210Tables *tab, uint8_t *tile, uint64_t stride, uint32_t len,
+                                 cudaStream_t stream);
+
 // Compaction of an odd-only bitmap into a prime list.
 constexpr uint32_t kCompactTileWords = 2048;  // 256 threads x 8 words
 cudaError_t launch_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *tile_counts,

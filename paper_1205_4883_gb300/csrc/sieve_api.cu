@@ -346,6 +346,111 @@ int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mo
                           (int)std::min<uint64_t>(n_mr, 4ull * ctx->num_sms), n_mr);
 }
 
+// Segment size of the mod-210 count path: the configured segment rounded down
+// to a multiple of 3 words (2 whole groups per 3 words).
+uint32_t w210_segment_words(const Params &prm) {
+    const uint32_t w = std::min(prm.seg_bytes, kW210MaxSegmentBytes) / 4;
+    return std::max<uint32_t>(w / 3 * 3, 3);
+}
+
+// One range on the mod-210 wheel: segments start at group lo / 210.
+RangeDesc plan_range210(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_words) {
+    RangeDesc r;
+    std::memset(&r, 0, sizeof r);
+    r.lo = lo;
+    r.hi = hi;
+    if (lo >= hi) return r;
+    r.Bbase = (int64_t)(lo / 210);
+    const uint64_t span = 210ull * (seg_words / 3 * 2);
+    r.nseg = (hi - 210ull * (uint64_t)r.Bbase + span - 1) / span;
+    r.n_use = primes_needed(primes, hi);
+    for (uint64_t q : {2, 3, 5, 7}) r.corr += lo <= q && q < hi;
+    return r;
+}
+
+// Plan a count-only launch of the m ranges in lb on the mod-210 wheel (no
+// bucket lists, no Miller-Rabin path): fills the launch header; *items_out is
+// the number of work items.
+int prepare_launch210(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t m, CursorStore *cs,
+                      uint64_t *items_out) {
+    const std::vector<uint32_t> &h = ctx->h_primes;
+    RangeDesc *rd = lb.h_ranges();
+    uint64_t segs = 0;
+    uint32_t nmax = 0;
+    for (size_t i = 0; i < m; ++i) {
+        segs += rd[i].nseg;
+        if (rd[i].nseg) nmax = std::max(nmax, rd[i].n_use);
+    }
+    const uint32_t sw = w210_segment_words(prm);
+    const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
+    const uint32_t small_end = std::max(kFirstCrossingPrime, first_at_least(h, prm.small_limit210));
+    // primes below words / 6 have at least two hits per sub-progression in a full segment
+    const uint32_t mid_lim = prm.mid_limit210 ? prm.mid_limit210 : std::max<uint32_t>(sw / 6, 23);
+    const uint32_t mid_end = std::max(small_end, first_at_least(h, mid_lim));
+    const uint32_t n_large = nmax > mid_end ? nmax - mid_end : 0;
+    const bool cursors = cs && n_large && h[nmax - 1] < (1u << 27) &&
+                         (uint64_t)grid * n_large * 4 <= (uint64_t)prm.cursor_mb << 20;
+    uint32_t C = 1;
+    if (cursors) {
+        C = prm.chunk_segs;
+        while (C > 1 && segs / C < 4 * grid) C /= 2;
+    }
+    uint64_t items = 0;
+    for (size_t i = 0; i < m; ++i) {
+        rd[i].item_first = items;
+        items += (rd[i].nseg + C - 1) / C;
+    }
+    SieveLaunch &L = *reinterpret_cast<SieveLaunch *>(lb.h_block);
+    std::memset(&L, 0, sizeof L);
+    L.ranges = lb.d_ranges();
+    L.n_ranges = (uint32_t)m;
+    L.n_items = items;
+    L.item_counter = lb.d_acc;
+    L.counts = lb.d_acc + 1;
+    L.overflow = reinterpret_cast<unsigned *>(lb.d_acc + m + 1);
+    L.primes = ctx->d_primes;
+    L.magic = ctx->d_magic;
+    L.seg_bytes = 4 * sw;
+    L.chunk_segs = C;
+    L.small_end = small_end;
+    L.mid_end = mid_end;
+    L.bucket_first = 0xffffffffu;
+    if (cursors && C > 1) {
+        const size_t need = (size_t)grid * n_large;
+        if (need > cs->entries) {
+            dev_free(ctx, cs->d, cs->entries);
+            cs->entries = 0;
+            int rc = dev_alloc(ctx, &cs->d, need);
+            if (rc) return rc;
+            cs->entries = need;
+        }
+        L.cursors = cs->d;
+        L.cursor_stride = n_large;
+    }
+    *items_out = items;
+    return SIEVE_OK;
+}
+
+// Block copy, accumulator clear and the mod-210 sieve over `grid` CTAs.
+int enqueue_launch210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, LaunchBuffers &lb, size_t m, int grid) {
+    CK(cudaMemcpyAsync(lb.d_block, lb.h_block, kLaunchHeader + m * sizeof(RangeDesc), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
+    if (grid > 0)
+        CK(launch_sieve210(reinterpret_cast<const SieveLaunch *>(lb.d_block), ctx->d_tab210, ctx->d_tile210,
+                           ctx->tile210_stride, grid, prm.threads, (4 * w210_segment_words(prm) + 15) & ~15u,
+                           stream));
+    return SIEVE_OK;
+}
+
+int launch_ranges210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, LaunchBuffers &lb, size_t m,
+                     CursorStore *cs) {
+    uint64_t items = 0;
+    int rc = prepare_launch210(ctx, prm, lb, m, cs, &items);
+    if (rc) return rc;
+    const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
+    return enqueue_launch210(ctx, stream, prm, lb, m, (int)std::min<uint64_t>(grid, items));
+}
+
 int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
                  uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64) {
     const uint64_t nwords = bitmap_words_of(lo, hi);
@@ -522,13 +627,16 @@ int bitmap_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, uin
 // launch parameters and range descriptors live in the pinned block that the
 // graph's first copy reads, so a replay only needs the block refreshed.
 // Batches that need bucket lists are launched directly (*used = false).
+constexpr int kModeCount210 = 2;  // graph key of count launches on the mod-210 wheel
+
 int batch_graph(sieve_ctx *ctx, int mode, size_t m, bool *used) {
     *used = false;
     const Params &prm = ctx->params;
     uint64_t items = 0;
-    int rc = prepare_launch(ctx, prm, mode, ctx->lb, m, nullptr, &ctx->cursors, &items);
+    int rc = mode == kModeCount210 ? prepare_launch210(ctx, prm, ctx->lb, m, &ctx->cursors, &items)
+                                   : prepare_launch(ctx, prm, mode, ctx->lb, m, nullptr, &ctx->cursors, &items);
     if (rc) return rc;
-    {
+    if (mode != kModeCount210) {
         const uint64_t blim = prm.bucket_limit ? prm.bucket_limit : prm.seg_bytes;
         uint32_t nmax = 0;
         for (size_t i = 0; i < m; ++i)
@@ -542,7 +650,9 @@ int batch_graph(sieve_ctx *ctx, int mode, size_t m, bool *used) {
         const int grid = ctx->num_sms * prm.ctas_per_sm;
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_launch(ctx, ctx->capture_stream, prm, mode, ctx->lb, m, grid, 4 * ctx->num_sms, m);
+        rc = mode == kModeCount210 ? enqueue_launch210(ctx, ctx->capture_stream, prm, ctx->lb, m, grid)
+                                   : enqueue_launch(ctx, ctx->capture_stream, prm, mode, ctx->lb, m, grid,
+                                                    4 * ctx->num_sms, m);
         cudaError_t e1 = cudaMemcpyAsync(ctx->lb.h_acc, ctx->lb.d_acc + 1, (m + 1) * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToHost, ctx->capture_stream);
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -611,6 +721,25 @@ int sieve_create(sieve_ctx **out, uint64_t hi_max, int device, void *cuda_stream
     if (rc) return bail(rc);
     e = launch_build_tile(ctx->d_tile, ctx->tile_stride, (uint32_t)len, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "build tile"));
+    // the mod-210 count path: class tables and the 16 shifted copies of its pattern
+    {
+        e = set_sieve210_smem_limit();
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaFuncSetAttribute"));
+        W210Tables t;
+        build_w210_tables(&t);
+        rc = dev_alloc(ctx, &ctx->d_tab210, 1);
+        if (rc) return bail(rc);
+        e = cudaMemcpyAsync(ctx->d_tab210, &t, sizeof t, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "copy tables"));
+        const uint64_t len210 = ((uint64_t)kW210PeriodBytes + kW210MaxSmemBytes + 32 + 15) & ~15ull;
+        ctx->tile210_stride = len210;
+        rc = dev_alloc(ctx, &ctx->d_tile210, len210 * kTileCopies);
+        if (rc) return bail(rc);
+        e = launch_build_tile210(ctx->d_tab210, ctx->d_tile210, ctx->tile210_stride, (uint32_t)len210, ctx->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "build tile"));
+        e = cudaStreamSynchronize(ctx->stream);  // t is on this stack frame
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "build tables"));
+    }
     rc = make_base_primes(ctx);
     if (rc) return bail(rc);
     *out = ctx;
@@ -626,6 +755,8 @@ void sieve_destroy(sieve_ctx *ctx) {
         cudaFree(ctx->d_primes);
         cudaFree(ctx->d_magic);
         cudaFree(ctx->d_tile);
+        cudaFree(ctx->d_tile210);
+        cudaFree(ctx->d_tab210);
     }
     cudaFree(ctx->d_bitmap);
     cudaFree(ctx->buckets.d);
@@ -649,6 +780,15 @@ int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count) {
     }
     rc = ensure_launch(ctx, 1);
     if (rc) return rc;
+    if (ctx->params.wheel == 210) {
+        ctx->lb.h_ranges()[0] = plan_range210(ctx->h_primes, lo, hi, w210_segment_words(ctx->params));
+        rc = launch_ranges210(ctx, ctx->stream, ctx->params, ctx->lb, 1, &ctx->cursors);
+        int of = 0;
+        if (!rc) rc = finish(ctx, ctx->lb, 1, &of);
+        if (rc) return rc;
+        *count = ctx->lb.h_acc[0];
+        return SIEVE_OK;
+    }
     ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeCount, nullptr);
     rc = run_sync(ctx, kModeCount, 1);
     if (rc) return rc;
@@ -663,8 +803,13 @@ int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_de
     if ((rc = set_device(ctx))) return rc;
     rc = ensure_launch(ctx, 1);
     if (rc) return rc;
-    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeCount, nullptr);
-    rc = launch_ranges(ctx, ctx->stream, ctx->params, kModeCount, ctx->lb, 1, &ctx->buckets, &ctx->cursors);
+    if (ctx->params.wheel == 210) {
+        ctx->lb.h_ranges()[0] = plan_range210(ctx->h_primes, lo, hi, w210_segment_words(ctx->params));
+        rc = launch_ranges210(ctx, ctx->stream, ctx->params, ctx->lb, 1, &ctx->cursors);
+    } else {
+        ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeCount, nullptr);
+        rc = launch_ranges(ctx, ctx->stream, ctx->params, kModeCount, ctx->lb, 1, &ctx->buckets, &ctx->cursors);
+    }
     if (rc) return rc;
     // the count, or UINT64_MAX if a bucket list overflowed
     CK(launch_finalize_count(ctx->lb.d_acc + 1, reinterpret_cast<const unsigned *>(ctx->lb.d_acc + 2), count_dev,
@@ -735,14 +880,17 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, si
     if (rc) return rc;
     rc = ensure_launch(ctx, m);
     if (rc) return rc;
-    const int mode = bitmaps_dev ? kModeBitmap : kModeCount;
+    const int mode = bitmaps_dev ? kModeBitmap : ctx->params.wheel == 210 ? kModeCount210 : kModeCount;
     for (size_t i = 0; i < m; ++i)
-        ctx->lb.h_ranges()[i] = plan_range(ctx->h_primes, lo[i], hi[i], ctx->params.seg_bytes, mode,
-                                           bitmaps_dev ? bitmaps_dev[i] : nullptr);
+        ctx->lb.h_ranges()[i] =
+            mode == kModeCount210
+                ? plan_range210(ctx->h_primes, lo[i], hi[i], w210_segment_words(ctx->params))
+                : plan_range(ctx->h_primes, lo[i], hi[i], ctx->params.seg_bytes, mode,
+                             bitmaps_dev ? bitmaps_dev[i] : nullptr);
     bool used = false;
     rc = batch_graph(ctx, mode, m, &used);
     if (rc) return rc;
-    if (!used) {
+    if (!used) {  // not reached for kModeCount210 (always captured)
         rc = run_sync(ctx, mode, m);
         if (rc) return rc;
     }
@@ -790,6 +938,18 @@ int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
             if (v < 0 || v > 1000000) return fail(ctx, SIEVE_EINVAL, "Miller-Rabin percent");
             p.mr_percent = (uint32_t)v;
             break;
+        case SIEVE_PARAM_WHEEL:
+            if (v != 30 && v != 210) return fail(ctx, SIEVE_EINVAL, "wheel (30 or 210)");
+            p.wheel = (int)v;
+            break;
+        case SIEVE_PARAM_SMALL_LIMIT_210:
+            if (v < 0 || v > (1 << 20)) return fail(ctx, SIEVE_EINVAL, "small limit (mod 210)");
+            p.small_limit210 = (uint32_t)v;
+            break;
+        case SIEVE_PARAM_MID_LIMIT_210:
+            if (v < 0 || v > (1ll << 31)) return fail(ctx, SIEVE_EINVAL, "mid limit (mod 210)");
+            p.mid_limit210 = (uint32_t)v;
+            break;
         default:
             return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
@@ -810,6 +970,9 @@ int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
         case SIEVE_PARAM_CURSOR_MB: *v = p.cursor_mb; return SIEVE_OK;
         case SIEVE_PARAM_MR_PERCENT: *v = p.mr_percent; return SIEVE_OK;
         case SIEVE_PARAM_MID_LIMIT: *v = p.mid_limit; return SIEVE_OK;
+        case SIEVE_PARAM_WHEEL: *v = p.wheel; return SIEVE_OK;
+        case SIEVE_PARAM_SMALL_LIMIT_210: *v = p.small_limit210; return SIEVE_OK;
+        case SIEVE_PARAM_MID_LIMIT_210: *v = p.mid_limit210; return SIEVE_OK;
         default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");
     }
 }
@@ -836,11 +999,13 @@ int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clea
     if (!clears) return fail(ctx, SIEVE_EINVAL, "null clears");
     int rc = check_range(ctx, lo, hi);
     if (rc) return rc;
-    // For each base prime p >= 23: #{ m : m >= p, gcd(m, 30) = 1, lo <= p m < hi }.
-    auto coprime30_below = [](uint64_t x) -> uint64_t {  // #{ 1 <= m < x : gcd(m, 30) = 1 }
-        static const uint8_t cum[30] = {0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 4,
-                                        4, 4, 4, 5, 5, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7};
-        return (x / 30) * 8 + cum[x % 30];
+    // For each base prime p >= 23: #{ m : m >= p, gcd(m, W) = 1, lo <= p m < hi }, W the
+    // wheel of the count path (30, or 210 when SIEVE_PARAM_WHEEL is 210).
+    const uint64_t W = ctx->params.wheel == 210 ? 210 : 30;
+    uint64_t cum[211] = {0};  // cum[r] = #{ 1 <= m < r : gcd(m, W) = 1 }
+    for (uint64_t r = 1; r <= W; ++r) cum[r] = cum[r - 1] + ((r - 1) % 2 && (r - 1) % 3 && (r - 1) % 5 && (W == 30 || (r - 1) % 7));
+    auto coprime_below = [&](uint64_t x) -> uint64_t {  // #{ 1 <= m < x : gcd(m, W) = 1 }
+        return (x / W) * cum[W] + cum[x % W];
     };
     uint64_t total = 0;
     const uint32_t n_use = primes_needed(ctx->h_primes, hi);
@@ -848,7 +1013,7 @@ int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clea
         const uint64_t p = ctx->h_primes[i];
         uint64_t m_lo = std::max<uint64_t>(p, (lo + p - 1) / p);
         uint64_t m_hi = (hi + p - 1) / p;  // m < m_hi  <=>  p m < hi
-        if (m_hi > m_lo) total += coprime30_below(m_hi) - coprime30_below(m_lo);
+        if (m_hi > m_lo) total += coprime_below(m_hi) - coprime_below(m_lo);
     }
     *clears = total;
     return SIEVE_OK;

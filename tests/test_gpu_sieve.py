@@ -147,6 +147,20 @@ def test_launch_parameters_do_not_change_results(seg, threads, small, ctas, chun
             assert np.array_equal(words.cpu().numpy().view(np.uint32), oracle.bitmap(lo, hi))
 
 
+@pytest.mark.parametrize("mid", [0, 2000, 400_000, 60])
+def test_tier_limits_do_not_change_results(mid):
+    # which primes go to the per-phase tier and which to the wheel walk; ranges around
+    # the squares of primes near 10^6 (999983^2) start those primes mid-segment
+    p2 = 999983 ** 2
+    with gb.Sieve(10**13) as s:
+        s.set_param(gb.SIEVE_PARAM_MID_LIMIT, mid)
+        for lo, hi in [(0, 10**8), (123_456_789_012, 123_456_789_012 + 3 * 10**6), (5, 40_000),
+                       (9 * 10**12, 9 * 10**12 + 2 * 10**7), (p2 - 5 * 10**6, p2 + 5 * 10**6)]:
+            assert s.count(lo, hi) == oracle.count(lo, hi), (lo, hi)
+            words, _ = s.bitmap(lo, hi)
+            assert np.array_equal(words.cpu().numpy().view(np.uint32), oracle.bitmap(lo, hi)), (lo, hi)
+
+
 def test_large_lo_against_miller_rabin(sv):
     lo, hi = 10**14, 10**14 + 60_000
     got = [int(v) for v in sv.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)]

@@ -172,3 +172,118 @@ def test_montgomery_miller_rabin_as_the_kernel_does_it():
         done += 1
     for n in (2152302898747, 3474749660383, 341550071728321):  # strong pseudoprimes to small bases
         assert not kernel_mr(n)
+
+
+# ---------------------------------------------------------------- mod-210 wheel
+R48 = [r for r in range(210) if r % 2 and r % 3 and r % 5 and r % 7]
+IDX48 = {r: i for i, r in enumerate(R48)}
+
+
+def _multiples210(p, G0, L):
+    """(group offset, class bit) of the multiples p m, m >= p, gcd(m, 210) = 1, in
+    groups [G0, G0 + L) -- the plain definition."""
+    out = []
+    m = max(p, (210 * G0 + p - 1) // p)
+    while p * m < 210 * (G0 + L):
+        if m % 2 and m % 3 and m % 5 and m % 7 and p * m >= 210 * G0:
+            out.append((p * m // 210 - G0, IDX48[p * m % 210]))
+        m += 1
+    return out
+
+
+def test_w210_tables_and_group0():
+    assert len(R48) == 48 and R48[0] == 1 and R48[1] == 11 and R48[-1] == 209
+    composite = [r for r in R48 if r == 1 or any(r % d == 0 for d in range(2, int(r ** 0.5) + 1))]
+    assert composite == [1, 121, 143, 169, 187, 209]
+    bits = sum(1 << i for i, r in enumerate(R48) if r not in composite)
+    assert bits & 0xFFFFFFFF == 0xF7FFFFFE and bits >> 32 == 0x7BBE
+
+
+def test_w210_first_class_closed_form():
+    # class j's first multiple of turn a = floor(G0 / p) lies before G0 iff c_j < R,
+    # c_j = floor(p r_j / 210), i.e. iff r_j <= floor((210 R - 1) / p)
+    rng = random.Random(11)
+    cnt = [sum(1 for r in R48 if r <= v) for v in range(210)]
+    primes = small_primes(200000)[5:]
+    for _ in range(3000):
+        p = rng.choice(primes)
+        R = rng.randrange(0, p)
+        want = sum(1 for r in R48 if p * r // 210 < R)
+        got = cnt[(210 * R - 1) // p] if R else 0
+        assert got == want, (p, R)
+
+
+def test_w210_step_table_walk_equals_the_definition():
+    rng = random.Random(12)
+    primes = small_primes(60000)[5:]
+    for _ in range(300):
+        p = rng.choice(primes)
+        L = rng.choice([64, 1024, 8192])
+        G0 = rng.choice([rng.randrange(0, 10**6), p * p // 210 - rng.randrange(0, 3 * p),
+                         rng.randrange(p * p // 210, p * p // 210 + 10**6)])
+        G0 = max(G0, 0)
+        pq, pr = divmod(p, 210)
+        pc = IDX48[pr]
+        # start: turn a = G0 // p, class k by the closed form, not before m = p
+        Q, R = divmod(G0, p)
+        k = sum(1 for r in R48 if r <= (210 * R - 1) // p) if R else 0
+        a = Q
+        if k == 48:
+            k, a = 0, a + 1
+        if a < pq or (a == pq and k < pc):
+            a, k = pq, pc
+        off = p * a + pq * R48[k] + (pr * R48[k]) // 210 - G0
+        got = []
+        while off < L:
+            rk, rk1 = R48[k], (R48[k + 1] if k < 47 else 211)
+            got.append((off, IDX48[pr * rk % 210]))
+            dadj = pr * rk1 // 210 - pr * rk // 210
+            assert 0 <= dadj <= 10 and 1 <= (rk1 - rk) // 2 <= 5
+            off += 2 * pq * ((rk1 - rk) // 2) + dadj
+            k = 0 if k == 47 else k + 1
+        assert got == _multiples210(p, G0, L), (p, G0, L)
+
+
+def test_w210_small_split_is_conflict_free_and_complete():
+    # class progression b0 + 48 p t (bits); lane l, e in {0, 1} takes t = s (mod 64) with
+    # 3 p s = 2 l + e - floor(b0 / 16) (mod 64): its words are l (mod 32), its bit 16 e + b0 mod 16
+    rng = random.Random(13)
+    for _ in range(400):
+        p = rng.choice([23, 29, 31, 97, 101, 127, 211, 509])
+        Lw = rng.choice([96, 1536, 57342])
+        b0 = rng.randrange(0, 32 * Lw)
+        a3 = 3 * p
+        inv = (a3 * (2 - a3 * a3)) & 63
+        assert (a3 * inv) % 64 == 1
+        uh, ul = (b0 >> 4) & 63, b0 & 15
+        got = []
+        for lane in range(32):
+            for e in range(2):
+                v = (2 * lane + e - uh) & 63
+                s = (v * inv) & 63
+                b = b0 + 48 * p * s
+                assert (b >> 5) % 32 == lane and b & 31 == 16 * e + ul
+                w = b >> 5
+                while w < Lw:
+                    got.append(32 * w + 16 * e + ul)
+                    w += 96 * p
+        assert sorted(got) == list(range(b0, 32 * Lw, 48 * p))
+
+
+def test_w210_medium_even_odd_split():
+    # the even and odd hits of a class progression (stride 96 p bits = 3 p words) keep
+    # one bit position each: b0 mod 32 and (b0 + 48 p) mod 32
+    rng = random.Random(14)
+    primes = small_primes(20000)[30:]
+    for _ in range(150):
+        p = rng.choice(primes)
+        Lw = rng.choice([96, 1536, 57342])
+        b0 = rng.randrange(0, 32 * Lw)
+        got = []
+        for e in range(2):
+            b = b0 + e * 48 * p
+            w = b >> 5
+            while w < Lw:
+                got.append(32 * w + (b & 31))
+                w += 3 * p
+        assert sorted(got) == list(range(b0, 32 * Lw, 48 * p))
