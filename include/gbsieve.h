@@ -257,6 +257,9 @@ void sieve_server_destroy(sieve_server *srv);
 #define SIEVE_PARAM_MID_LIMIT_210 12 /* mod-210 wheel: primes from the small limit up to this are
                                         crossed one lane per prime with per-class sub-progressions,
                                         larger ones by the wheel walk (0 = segment words / 6) */
+#define SIEVE_PARAM_BATCH_ORDER   13 /* sieve_batch_count launches the ranges in the given order
+                                        (0, default), heaviest first by estimated work (1), or
+                                        heaviest and lightest alternating (2); results are the same */
 #define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
                                        primes, carried across the segments of a work item; used
                                        when they fit (default 64; 0 = recompute per segment) */

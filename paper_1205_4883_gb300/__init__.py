@@ -38,6 +38,7 @@ SIEVE_PARAM_MID_LIMIT = 9
 SIEVE_PARAM_WHEEL = 10
 SIEVE_PARAM_SMALL_LIMIT_210 = 11
 SIEVE_PARAM_MID_LIMIT_210 = 12
+SIEVE_PARAM_BATCH_ORDER = 13
 
 _u64 = ctypes.c_uint64
 _i64 = ctypes.c_int64
@@ -443,7 +444,8 @@ class Sieve:
                   "chunk_segments": SIEVE_PARAM_CHUNK_SEGMENTS, "bucket_limit": SIEVE_PARAM_BUCKET_LIMIT,
                   "cursor_mb": SIEVE_PARAM_CURSOR_MB, "mr_percent": SIEVE_PARAM_MR_PERCENT,
                   "mid_limit": SIEVE_PARAM_MID_LIMIT, "wheel": SIEVE_PARAM_WHEEL,
-                  "small_limit_210": SIEVE_PARAM_SMALL_LIMIT_210, "mid_limit_210": SIEVE_PARAM_MID_LIMIT_210}
+                  "small_limit_210": SIEVE_PARAM_SMALL_LIMIT_210, "mid_limit_210": SIEVE_PARAM_MID_LIMIT_210,
+                  "batch_order": SIEVE_PARAM_BATCH_ORDER}
 
     def apply_plan(self, plan: dict) -> None:
         """Set the launch parameters of an autotuned plan (see autotune.py)."""

@@ -26,6 +26,7 @@ struct Params {
     int wheel = 30;                      // count-only launches on the mod-30 or the mod-210 wheel
     uint32_t small_limit210 = 128;       // mod-210: primes below this are crossed warp-cooperatively
     uint32_t mid_limit210 = 0;           // mod-210: primes below this use per-class sub-progressions; 0: words / 6
+    int batch_order = 0;                 // batches: 0 as given, 1 heaviest first, 2 heaviest/lightest alternating
 };
 
 // Everything one sieve launch reads and writes besides the resident state:
@@ -105,6 +106,7 @@ struct sieve_ctx {
     gbs::BucketStore buckets;
     gbs::CursorStore cursors;
     gbs::MrScratch mr;
+    std::vector<uint32_t> batch_order;  // launch position -> caller's index, last batch
     uint32_t *d_bitmap = nullptr;  // list scratch
     size_t bitmap_cap = 0;         // words
 

@@ -881,12 +881,37 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, si
     rc = ensure_launch(ctx, m);
     if (rc) return rc;
     const int mode = bitmaps_dev ? kModeBitmap : ctx->params.wheel == 210 ? kModeCount210 : kModeCount;
-    for (size_t i = 0; i < m; ++i)
-        ctx->lb.h_ranges()[i] =
-            mode == kModeCount210
-                ? plan_range210(ctx->h_primes, lo[i], hi[i], w210_segment_words(ctx->params))
-                : plan_range(ctx->h_primes, lo[i], hi[i], ctx->params.seg_bytes, mode,
-                             bitmaps_dev ? bitmaps_dev[i] : nullptr);
+    auto plan = [&](size_t i) {
+        return mode == kModeCount210 ? plan_range210(ctx->h_primes, lo[i], hi[i], w210_segment_words(ctx->params))
+                                     : plan_range(ctx->h_primes, lo[i], hi[i], ctx->params.seg_bytes, mode,
+                                                  bitmaps_dev ? bitmaps_dev[i] : nullptr);
+    };
+    // Launch order (SIEVE_PARAM_BATCH_ORDER): as given, heaviest first, or heaviest
+    // and lightest alternating -- GPU forms of sieving the last blocks from both
+    // ends, since persistent CTAs take work items in launch order.  Estimated work
+    // of a range: every segment visits its n_use base primes (about 3 warp
+    // instructions each) and crosses 0.16 warp instructions per integer.
+    std::vector<uint32_t> &order = ctx->batch_order;
+    order.resize(m);
+    for (size_t i = 0; i < m; ++i) order[i] = (uint32_t)i;
+    if (ctx->params.batch_order) {
+        std::vector<double> cost(m);
+        for (size_t i = 0; i < m; ++i) {
+            const RangeDesc r = plan(i);
+            cost[i] = 3.0 * (double)r.nseg * r.n_use + 0.16 * (double)(hi[i] - lo[i]);
+        }
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+        if (ctx->params.batch_order == 2) {  // heaviest, lightest, second heaviest, ...
+            std::vector<uint32_t> mixed;
+            mixed.reserve(m);
+            for (size_t a = 0, b = m; a < b;) {
+                mixed.push_back(order[a++]);
+                if (a < b) mixed.push_back(order[--b]);
+            }
+            order.swap(mixed);
+        }
+    }
+    for (size_t k = 0; k < m; ++k) ctx->lb.h_ranges()[k] = plan(order[k]);
     bool used = false;
     rc = batch_graph(ctx, mode, m, &used);
     if (rc) return rc;
@@ -894,7 +919,7 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, si
         rc = run_sync(ctx, mode, m);
         if (rc) return rc;
     }
-    for (size_t i = 0; i < m; ++i) counts[i] = ctx->lb.h_acc[i];
+    for (size_t k = 0; k < m; ++k) counts[order[k]] = ctx->lb.h_acc[k];
     return SIEVE_OK;
 }
 
@@ -942,6 +967,10 @@ int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
             if (v != 30 && v != 210) return fail(ctx, SIEVE_EINVAL, "wheel (30 or 210)");
             p.wheel = (int)v;
             break;
+        case SIEVE_PARAM_BATCH_ORDER:
+            if (v < 0 || v > 2) return fail(ctx, SIEVE_EINVAL, "batch order (0, 1 or 2)");
+            p.batch_order = (int)v;
+            break;
         case SIEVE_PARAM_SMALL_LIMIT_210:
             if (v < 0 || v > (1 << 20)) return fail(ctx, SIEVE_EINVAL, "small limit (mod 210)");
             p.small_limit210 = (uint32_t)v;
@@ -971,6 +1000,7 @@ int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
         case SIEVE_PARAM_MR_PERCENT: *v = p.mr_percent; return SIEVE_OK;
         case SIEVE_PARAM_MID_LIMIT: *v = p.mid_limit; return SIEVE_OK;
         case SIEVE_PARAM_WHEEL: *v = p.wheel; return SIEVE_OK;
+        case SIEVE_PARAM_BATCH_ORDER: *v = p.batch_order; return SIEVE_OK;
         case SIEVE_PARAM_SMALL_LIMIT_210: *v = p.small_limit210; return SIEVE_OK;
         case SIEVE_PARAM_MID_LIMIT_210: *v = p.mid_limit210; return SIEVE_OK;
         default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");

@@ -255,6 +255,20 @@ def test_batch_4096_intervals(sv):
             assert counts[i] == oracle.count(los[i], his[i]), i
 
 
+def test_batch_order_does_not_change_results(sv):
+    los, his = batch_intervals(512, seed=77)
+    assert sv.get_param(gb.SIEVE_PARAM_BATCH_ORDER) == 0
+    as_given = sv.batch_count(los, his)
+    try:
+        for order in (1, 2):
+            sv.set_param(gb.SIEVE_PARAM_BATCH_ORDER, order)
+            assert sv.batch_count(los, his) == as_given, order
+    finally:
+        sv.set_param(gb.SIEVE_PARAM_BATCH_ORDER, 0)
+    for i in range(0, 512, 61):
+        assert as_given[i] == sv.count(los[i], his[i])
+
+
 def test_batch_with_bitmaps(sv):
     los, his = batch_intervals(64, seed=11, lo_exp=(3, 13), w_exp=(1, 6))
     bms = [torch.zeros(max(gb.sieve_bitmap_words(a, b), 1), dtype=torch.int32, device="cuda") if i % 3 else None
