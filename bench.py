@@ -10,6 +10,11 @@ With N > 1 (torchrun, one rank per GPU) each rank sieves its own block of
 10^12 integers, [r 10^12, (r + 1) 10^12): independent units, no collective
 on the data path (weak scaling).  --impl reference times the CPU oracle on
 the host cores on a bounded sample of the same workload.
+
+Other workloads (one GPU, one JSON line each): --workload batched (4096
+intervals, one launch), served (a Poisson request stream through the
+server), range2p32 (odd-only bitmap and u32 list of [0, 2^32)) and pi1e7
+(count, bitmap and list of [0, 10^7)).
 """
 from __future__ import annotations
 
@@ -200,8 +205,7 @@ def run_gpu(args):
     expect = sv.count(lo, hi)
 
     props = torch.cuda.get_device_properties(dev)
-    gpu_id = getattr(props, "uuid", None)
-    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else str(gpu_id or dev)
+    gpu_id = _gpu_id(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
@@ -276,6 +280,13 @@ def run_gpu(args):
     return line
 
 
+def _gpu_id(dev):
+    """nvidia-smi's name for CUDA device `dev` (its UUID; the index if unknown)."""
+    import torch
+    u = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    return f"GPU-{u}" if u is not None and not str(u).startswith("GPU-") else str(u or dev)
+
+
 def _event_ms(fn, reps):
     import torch
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -322,6 +333,87 @@ def run_batched(args):
             "one_call_per_interval": {"value": units / one_by_one, "unit": METRIC},
             "plain_single_range": {"value": 10**10 / (plain_ms * 1e-3), "unit": METRIC,
                                    "range": "[1e14, 1e14 + 1e10)"}}
+    sv.close()
+    print(json.dumps(line))
+    return 0
+
+
+def run_outputs(args, lo, hi, name, with_count):
+    """One range's outputs through the C ABI into preallocated device buffers: (optionally the
+    count,) the odd-only bitmap (sieve_bitmap) and the prime list compacted from it
+    (sieve_compact, u32).  Per stage: CUDA-event time on the context's stream.  The bitmap
+    stage is the sieve kernel (bit-clears against the shared-memory op peak); the list stage
+    reads the bitmap twice and writes the list (HBM).  e2e adds the copy of the list to pinned
+    host memory."""
+    import torch
+    import paper_1205_4883_gb300 as gb
+    torch.cuda.set_device(0)
+    sv = gb.Sieve(hi)
+    stream = torch.cuda.current_stream()
+    nw = gb.sieve_bitmap_words(lo, hi)
+    n = sv.count(lo, hi)
+    bm = torch.empty(nw, dtype=torch.int32, device="cuda")
+    lst = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    host = torch.empty(max(n, 1), dtype=torch.int32, pin_memory=True)
+    flush = torch.empty(256 * 2**20, dtype=torch.uint8, device="cuda")
+
+    def stages(evs):
+        if with_count:
+            sv.count(lo, hi)
+        evs[0].record(stream)
+        c = gb.sieve_bitmap(sv.ctx, lo, hi, bm)
+        evs[1].record(stream)
+        k, rc = gb.sieve_compact(sv.ctx, bm, lo, hi, lst)
+        evs[2].record(stream)
+        return c, k
+
+    for _ in range(args.warmup):
+        stages([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    with ClockSampler(_gpu_id(torch.cuda.current_device())) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            c, got = stages(evs[k])
+        torch.cuda.synchronize()
+    assert c == n and got == n
+    t_bm = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    t_ls = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    # end to end: count (if asked), bitmap, list, and the list copied to pinned host memory
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        stages([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+        host.copy_(lst, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    peaks, peak_kind = _peaks()
+    props = torch.cuda.get_device_properties(0)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = props.multi_processor_count * 32 * sm_max * 1e6
+    clears = sv.crossing_work(lo, hi)
+    list_bytes = 4 * n + 4 * nw  # the list written, the bitmap read once (a second read is not credited)
+    hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
+    bm_line = {"bound": "alu", "op": "shared-memory bit-clear (atom.shared.and)", "kernel": "k_sieve<1>",
+               "achieved": clears / (t_bm * 1e-3) / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+               "frac": clears / (t_bm * 1e-3) / peak_ops, "traffic": None, "work_per_launch": clears,
+               "bitmap_bytes_written": 4 * nw}
+    ls_line = {"bound": "hbm", "kernel": "k_tile_popc + k_tile_scan + k_emit (sieve_compact)",
+               "achieved": list_bytes / (t_ls * 1e-3) / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+               "frac": list_bytes / (t_ls * 1e-3) / hbm, "traffic": None, "bytes_per_call": list_bytes,
+               "peak_basis": f"{peak_kind} hbm_gbs (copy, read + write)"}
+    dominant = bm_line if t_bm >= t_ls else ls_line
+    line = {"metric": METRIC, "value": (hi - lo) / ((t_bm + t_ls) * 1e-3), "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_bm + t_ls, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": name, "lo": lo, "hi": hi, "primes": n, "bitmap_words": nw,
+                       "l2": "flushed between steps (256 MiB write, untimed); outputs larger than L2"},
+            "stages_ms": {"bitmap": t_bm, "list": t_ls},
+            "roofline": dominant, "roofline_list": ls_line, "roofline_bitmap": bm_line,
+            "clocks": clk.summary(),
+            "e2e": {"value": (hi - lo) / e2e_s, "unit": METRIC, "h2d_bytes_per_step": 72,
+                    "d2h_bytes_per_step": 4 * n + 8},
+            "gpu_launches": args.steps * 5}
     sv.close()
     print(json.dumps(line))
     return 0
@@ -430,8 +522,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lo", type=int, default=0, help="with --hi: sieve [lo, hi) of each rank's block instead")
     ap.add_argument("--hi", type=int, default=None)
-    ap.add_argument("--workload", default="pi1e12", choices=["pi1e12", "batched", "served"],
-                    help="pi1e12 (default, the headline line), batched or served")
+    ap.add_argument("--workload", default="pi1e12", choices=["pi1e12", "batched", "served", "range2p32", "pi1e7"],
+                    help="pi1e12 (default, the headline line), batched, served, range2p32 (bitmap and "
+                         "u32 list of [0, 2^32)) or pi1e7 (count, bitmap and list of [0, 10^7))")
     ap.add_argument("--rates", default="100,300,1000,3000,10000", help="served: offered loads, req/s")
     ap.add_argument("--requests", type=int, default=0,
                     help="served: requests per rate (0: 1 s of arrivals, between 300 and 10000)")
@@ -444,6 +537,10 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "range2p32":
+        return run_outputs(args, 0, 1 << 32, "[0, 2^32): odd-only bitmap and u32 prime list", False)
+    if args.workload == "pi1e7":
+        return run_outputs(args, 0, 10**7, "[0, 10^7): count, odd-only bitmap and u32 prime list", True)
     line = run_gpu(args)
     ws, rank, _ = _dist()
     if rank == 0 and line is not None:

@@ -749,100 +749,6 @@ __global__ void k_magic(const uint32_t *primes, uint64_t *magic, uint64_t n) {
 
 // ---------------------------------------------------------------- compaction
 
-__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t *s_warp, uint32_t *total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    uint32_t wbase = 0, all = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        if (w < warp) wbase += s_warp[w];
-        all += s_warp[w];
-    }
-    *total = all;
-    return wbase + x - v;
-}
-
-__global__ void __launch_bounds__(256) k_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *tile_counts,
-                                                   uint64_t ntiles) {
-    __shared__ uint32_t s_warp[8];
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t w0 = t * kCompactTileWords + threadIdx.x * 8ull;
-        uint32_t c = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (w0 + k < nwords) c += __popc(__ldg(bitmap + w0 + k));
-        uint32_t total;
-        block_exclusive_scan_256(c, s_warp, &total);
-        if (threadIdx.x == 0) tile_counts[t] = total;
-        __syncthreads();
-    }
-}
-
-__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t *tile_counts, uint64_t *tile_offsets,
-                                                    uint64_t ntiles, unsigned long long *total) {
-    __shared__ unsigned long long s_warp[32];
-    __shared__ unsigned long long s_run;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_run = 0;
-    __syncthreads();
-    for (uint64_t base = 0; base < ntiles; base += blockDim.x) {
-        const uint64_t t = base + threadIdx.x;
-        const unsigned long long v = t < ntiles ? tile_counts[t] : 0ull;
-        unsigned long long x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        unsigned long long wbase = 0, all = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            if (w < warp) wbase += s_warp[w];
-            all += s_warp[w];
-        }
-        if (t < ntiles) tile_offsets[t] = s_run + wbase + x - v;
-        __syncthreads();
-        if (threadIdx.x == 0) s_run += all;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *total = s_run;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets,
-                                              uint64_t ntiles, uint64_t o0, uint32_t base_index, T *out) {
-    __shared__ uint32_t s_warp[8];
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t w0 = t * kCompactTileWords + threadIdx.x * 8ull;
-        uint32_t w[8];
-        uint32_t c = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            w[k] = (w0 + k < nwords) ? __ldg(bitmap + w0 + k) : 0u;
-            c += __popc(w[k]);
-        }
-        uint32_t total;
-        uint64_t pos = base_index + tile_offsets[t] + block_exclusive_scan_256(c, s_warp, &total);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            uint32_t v = w[k];
-            while (v) {
-                const int b = __ffs(v) - 1;
-                v &= v - 1;
-                out[pos++] = (T)(o0 + 2ull * ((w0 + k) * 32ull + b));
-            }
-        }
-        __syncthreads();
-    }
-}
-
 template <typename T>
 __global__ void k_put_two(T *out) { out[0] = (T)2; }
 
@@ -894,32 +800,6 @@ cudaError_t launch_magic(const uint32_t *primes, uint64_t *magic, uint64_t n, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *tile_counts, uint64_t ntiles,
-                             int grid, cudaStream_t stream) {
-    if (ntiles == 0) return cudaSuccess;
-    unsigned g = (unsigned)(ntiles < (uint64_t)grid ? ntiles : (uint64_t)grid);
-    k_tile_popc<<<g, 256, 0, stream>>>(bitmap, nwords, tile_counts, ntiles);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint64_t ntiles,
-                             unsigned long long *total, cudaStream_t stream) {
-    k_tile_scan<<<1, 1024, 0, stream>>>(tile_counts, tile_offsets, ntiles, total);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets, uint64_t ntiles,
-                        uint64_t o0, uint32_t base_index, void *out, int out64, int grid, cudaStream_t stream) {
-    if (ntiles == 0) return cudaSuccess;
-    unsigned g = (unsigned)(ntiles < (uint64_t)grid ? ntiles : (uint64_t)grid);
-    if (out64)
-        k_emit<uint64_t><<<g, 256, 0, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
-                                                static_cast<uint64_t *>(out));
-    else
-        k_emit<uint32_t><<<g, 256, 0, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
-                                                static_cast<uint32_t *>(out));
-    return cudaGetLastError();
-}
 
 cudaError_t launch_finalize_count(const unsigned long long *count, const unsigned *overflow, uint64_t *out,
                                   cudaStream_t stream) {
