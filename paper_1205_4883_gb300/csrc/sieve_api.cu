@@ -491,12 +491,30 @@ int finish(sieve_ctx *ctx, LaunchBuffers &lb, size_t m, int *overflowed) {
     return SIEVE_OK;
 }
 
+// Launch parameters for one range [lo, hi).  When the range has at most 8 waves
+// of full segments over the grid, the segment is shortened (in 32-byte steps,
+// not below 4 KB) so that the segments fill whole waves: otherwise the last
+// wave runs a few segments while the other CTAs wait.
+Params single_range_params(const sieve_ctx *ctx, uint64_t lo, uint64_t hi) {
+    Params p = ctx->params;
+    if (hi <= lo) return p;
+    const uint64_t grid = (uint64_t)ctx->num_sms * p.ctas_per_sm;
+    const uint64_t bytes = (hi - lo) / 30 + 64;  // wheel bytes, plus the grid origin's slack
+    const uint64_t n0 = (bytes + p.seg_bytes - 1) / p.seg_bytes;
+    if (n0 > 8 * grid) return p;
+    const uint64_t waves = (n0 + grid - 1) / grid;
+    uint64_t sb = (bytes + waves * grid - 1) / (waves * grid);
+    sb = std::max<uint64_t>((sb + 31) & ~31ull, 4096);
+    if (sb < p.seg_bytes) p.seg_bytes = (uint32_t)sb;
+    return p;
+}
+
 // launch + finish on the context's stream, re-running with larger bucket lists
 // if one overflowed (never expected: the margin is far above the spread of the
 // hit counts).  Counts are left in ctx->lb.h_acc[0..m).
-int run_sync(sieve_ctx *ctx, int mode, size_t m) {
+int run_sync(sieve_ctx *ctx, const Params &prm, int mode, size_t m) {
     for (int attempt = 0; attempt < 4; ++attempt) {
-        int rc = launch_ranges(ctx, ctx->stream, ctx->params, mode, ctx->lb, m, &ctx->buckets, &ctx->cursors);
+        int rc = launch_ranges(ctx, ctx->stream, prm, mode, ctx->lb, m, &ctx->buckets, &ctx->cursors);
         if (rc) return rc;
         int of = 0;
         rc = finish(ctx, ctx->lb, m, &of);
@@ -532,7 +550,7 @@ int primes_upto(sieve_ctx *ctx, uint64_t limit, uint32_t **out_dev, std::vector<
     rc = ensure_bitmap(ctx, bitmap_words_of(0, hi));
     if (rc) return rc;
     ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, 0, hi, ctx->params.seg_bytes, kModeBitmap, ctx->d_bitmap);
-    rc = run_sync(ctx, kModeBitmap, 1);
+    rc = run_sync(ctx, ctx->params, kModeBitmap, 1);
     if (rc) return rc;
     uint64_t n = 0;
     rc = compact_with(ctx, ctx->stream, ctx->cs, ctx->d_bitmap, 0, hi, nullptr, 0, &n, 0);
@@ -614,8 +632,9 @@ int set_device(sieve_ctx *ctx) {
 int bitmap_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, uint64_t *count) {
     int rc = ensure_launch(ctx, 1);
     if (rc) return rc;
-    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeBitmap, out_dev);
-    rc = run_sync(ctx, kModeBitmap, 1);
+    const Params prm = single_range_params(ctx, lo, hi);
+    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, prm.seg_bytes, kModeBitmap, out_dev);
+    rc = run_sync(ctx, prm, kModeBitmap, 1);
     if (rc) return rc;
     if (count) *count = ctx->lb.h_acc[0];
     return SIEVE_OK;
@@ -789,8 +808,9 @@ int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count) {
         *count = ctx->lb.h_acc[0];
         return SIEVE_OK;
     }
-    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeCount, nullptr);
-    rc = run_sync(ctx, kModeCount, 1);
+    const Params prm = single_range_params(ctx, lo, hi);
+    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, prm.seg_bytes, kModeCount, nullptr);
+    rc = run_sync(ctx, prm, kModeCount, 1);
     if (rc) return rc;
     *count = ctx->lb.h_acc[0];
     return SIEVE_OK;
@@ -807,8 +827,9 @@ int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_de
         ctx->lb.h_ranges()[0] = plan_range210(ctx->h_primes, lo, hi, w210_segment_words(ctx->params));
         rc = launch_ranges210(ctx, ctx->stream, ctx->params, ctx->lb, 1, &ctx->cursors);
     } else {
-        ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, ctx->params.seg_bytes, kModeCount, nullptr);
-        rc = launch_ranges(ctx, ctx->stream, ctx->params, kModeCount, ctx->lb, 1, &ctx->buckets, &ctx->cursors);
+        const Params prm = single_range_params(ctx, lo, hi);
+        ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, prm.seg_bytes, kModeCount, nullptr);
+        rc = launch_ranges(ctx, ctx->stream, prm, kModeCount, ctx->lb, 1, &ctx->buckets, &ctx->cursors);
     }
     if (rc) return rc;
     // the count, or UINT64_MAX if a bucket list overflowed
@@ -916,7 +937,7 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, si
     rc = batch_graph(ctx, mode, m, &used);
     if (rc) return rc;
     if (!used) {  // not reached for kModeCount210 (always captured)
-        rc = run_sync(ctx, mode, m);
+        rc = run_sync(ctx, ctx->params, mode, m);
         if (rc) return rc;
     }
     for (size_t k = 0; k < m; ++k) counts[order[k]] = ctx->lb.h_acc[k];
