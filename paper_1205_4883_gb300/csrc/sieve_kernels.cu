@@ -592,51 +592,39 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                     cnt += __popc(v);
                 }
             } else {
-                // 4'. expand each group of 32 wheel bytes (960 integers) into 15
-                //     words of the odd-only bitmap and store them
+                // 4'. each group of 32 wheel bytes (960 integers) is 15 words of the
+                //     odd-only bitmap: bits [32 q, 32 q + 32) of the group's 480 odd
+                //     positions, i.e. of the 15-bit expansions of its bytes
+                //     floor(32 q / 15) .. + 3, shifted by 32 q mod 15.  One thread per
+                //     output word, so a warp stores 32 consecutive words.
                 const uint64_t nwords = rd.bitmap_words;
                 const uint64_t o0 = rd.lo | 1;
                 const uint64_t nbits = o0 < rd.hi ? (rd.hi - o0 + 1) / 2 : 0;
                 uint32_t *out = rd.bitmap;
-                for (uint32_t gr = tid; gr < L / 32; gr += blockDim.x) {
-                    const int64_t n0 = base_int + 960 * (int64_t)gr + 1;  // first odd integer of the group
-                    const int64_t w0 = (n0 - (int64_t)o0) / 64;          // exact: n0 = o0 (mod 64)
-                    if (w0 + 15 <= 0 || w0 >= (int64_t)nwords) continue;
-                    uint32_t wv[8];
-                    const uint4 a = smem4[2 * gr], b = smem4[2 * gr + 1];
-                    wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
-                    wv[4] = b.x; wv[5] = b.y; wv[6] = b.z; wv[7] = b.w;
-                    uint32_t o[15];
-#pragma unroll
-                    for (int q = 0; q < 15; ++q) o[q] = 0;
-#pragma unroll
-                    for (int bb = 0; bb < 32; ++bb) {
-                        const uint32_t e = tab.expand[(wv[bb >> 2] >> (8 * (bb & 3))) & 0xffu];
-                        const int pos = 15 * bb, wi = pos >> 5, sh = pos & 31;
-                        o[wi] |= e << sh;
-                        if (sh > 17) o[wi + 1] |= e >> (32 - sh);
-                    }
+                const int64_t wbase = (base_int + 1 - (int64_t)o0) / 64;  // exact: the grid keeps n0 = o0 (mod 64)
+                const uint32_t nout = (L / 32) * 15;
+                for (uint32_t k = tid; k < nout; k += blockDim.x) {
+                    const int64_t wq = wbase + k;
+                    if (wq < 0 || wq >= (int64_t)nwords) continue;
+                    const uint32_t gr = k / 15, q = k - 15 * gr;
+                    const uint32_t b0 = 32 * gr + (32 * q) / 15, sh = (32 * q) % 15;
+                    uint64_t e = (uint64_t)tab.expand[seg[b0]] | (uint64_t)tab.expand[seg[b0 + 1]] << 15 |
+                                 (uint64_t)tab.expand[seg[b0 + 2]] << 30;
+                    // sh = 14 (q = 7 only) reaches bit 45: bit 0 of byte b0 + 3 = 17 of the group
+                    if (sh == 14) e |= (uint64_t)tab.expand[seg[b0 + 3]] << 45;
+                    uint32_t v = (uint32_t)(e >> sh);
                     // 3 and 5 are prime but have no wheel bit
+                    const int64_t n0 = base_int + 960 * (int64_t)gr + 1;  // first odd integer of the group
                     if (n0 <= 5 && n0 + 958 >= 3) {
 #pragma unroll
                         for (int sp = 3; sp <= 5; sp += 2) {
-                            const int64_t k = (sp - n0) / 2;
-                            if (sp >= n0 && k < 480) {
-#pragma unroll
-                                for (int q = 0; q < 15; ++q)  // compile-time register index
-                                    if ((k >> 5) == q) o[q] |= 1u << (k & 31);
-                            }
+                            const int64_t i = (sp - n0) / 2;  // odd position in the group
+                            if (sp >= n0 && (i >> 5) == (int64_t)q) v |= 1u << (i & 31);
                         }
                     }
-#pragma unroll
-                    for (int q = 0; q < 15; ++q) {
-                        const int64_t wq = w0 + q;
-                        if (wq < 0 || wq >= (int64_t)nwords) continue;
-                        uint32_t v = o[q];
-                        if (wq == (int64_t)nwords - 1 && (nbits & 31)) v &= (1u << (nbits & 31)) - 1u;
-                        if (out) out[wq] = v;
-                        cnt += __popc(v);
-                    }
+                    if (wq == (int64_t)nwords - 1 && (nbits & 31)) v &= (1u << (nbits & 31)) - 1u;
+                    if (out) out[wq] = v;
+                    cnt += __popc(v);
                 }
             }
             cnt = warp_sum(cnt);

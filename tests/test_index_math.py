@@ -287,3 +287,26 @@ def test_w210_medium_even_odd_split():
                 got.append(32 * w + (b & 31))
                 w += 3 * p
         assert sorted(got) == list(range(b0, 32 * Lw, 48 * p))
+
+
+def test_bitmap_words_from_wheel_byte_expansions():
+    # odd-only word q of a 32-byte wheel group = bits [32 q, 32 q + 32) of the bytes'
+    # 15-bit expansions laid end to end: bytes floor(32 q / 15) .. + 2, and + 3 when
+    # 32 q mod 15 = 14 (q = 7), never past the group's byte 31
+    rng = random.Random(15)
+    for _ in range(200):
+        group = [rng.randrange(256) for _ in range(32)]
+        stream = 0
+        for b, byte in enumerate(group):  # 15-bit expansion: bit (r - 1) / 2 for each residue present
+            e = sum(1 << ((RES[k] - 1) // 2) for k in range(8) if byte >> k & 1)
+            stream |= e << (15 * b)
+        for q in range(15):
+            b0, sh = divmod(32 * q, 15)
+            need = 4 if sh == 14 else 3
+            assert b0 + need - 1 <= 31 and (sh + 31 < 15 * need)
+            part = 0
+            for j in range(need):
+                byte = group[b0 + j]
+                e = sum(1 << ((RES[k] - 1) // 2) for k in range(8) if byte >> k & 1)
+                part |= e << (15 * j)
+            assert (part >> sh) & 0xFFFFFFFF == (stream >> (32 * q)) & 0xFFFFFFFF, q
