@@ -199,7 +199,9 @@ typedef struct {
     int32_t kind;
     uint64_t count;         /* primes in [lo, hi) */
     const uint64_t *primes; /* SIEVE_REQ_LIST: `count` primes, host memory owned by the
-                               server, valid until sieve_server_release; else NULL */
+                               server, valid until sieve_server_release; else NULL.  It is
+                               pinned memory (a 1 GiB arena the results are copied into by
+                               DMA) unless the arena was full, then ordinary heap memory */
     double latency_us;      /* from submit to the result being ready on the host */
 } sieve_result;
 

@@ -11,8 +11,9 @@
 // already queued while the current one runs.  When a tick's event has fired,
 // its counts are added to their requests; a request whose last run is done is
 // completed; a finished list request is handed to a second host thread that
-// compacts its bitmap on its own stream and copies the primes out through a
-// pinned bounce buffer, so the scheduler keeps launching ticks meanwhile.
+// compacts its bitmap on its own stream and copies the primes by DMA into a
+// pinned host arena (through a pinned bounce buffer to the heap when the arena
+// is full), so the scheduler keeps launching ticks meanwhile.
 // Host waits poll events and condition variables; no kernel waits on anything.
 
 #include <algorithm>
@@ -47,7 +48,9 @@ struct Req {
     uint64_t *d_list = nullptr;
     uint64_t list_cap = 0;
     size_t arena_off = 0, arena_bytes = 0;
-    std::unique_ptr<uint64_t[]> primes;  // list result (count entries)
+    std::unique_ptr<uint64_t[]> primes;  // list result on the heap (when the pinned arena is full)
+    uint64_t *h_primes = nullptr;        // the list result handed out: pinned arena or `primes`
+    size_t harena_off = 0, harena_bytes = 0;
     int status = SIEVE_OK;
     bool done = false;
     Clock::time_point t_submit;
@@ -66,7 +69,8 @@ struct Tick {
     bool busy = false;
 };
 
-// First-fit allocator over one device arena (offsets, 256-byte aligned).
+// First-fit allocator over one arena (offsets, 256-byte aligned): the device
+// arena of bitmaps and device lists, and the pinned host arena of list results.
 struct Arena {
     unsigned char *base = nullptr;
     size_t size = 0, used = 0;
@@ -123,6 +127,7 @@ struct sieve_server {
     bool finisher_stop = false;
     std::thread finisher;
     uint64_t *h_bounce = nullptr;      // pinned, kBounceWords
+    Arena host_arena;                  // pinned: list results, copied in by DMA, freed on release
 
     std::map<uint64_t, std::unique_ptr<Req>> reqs;
     std::deque<Req *> active;  // admitted, segments left to schedule or in flight
@@ -165,16 +170,34 @@ void complete(sieve_server *srv, Req *r, int status) {
 }
 
 constexpr size_t kBounceWords = 8u << 20;  // 64 MiB of uint64
+constexpr size_t kHostArenaBytes = 1ull << 30;  // pinned host memory for list results
 
 // Called without the lock: compaction of a finished list request into its
-// device list, then a chunked copy to host memory through the pinned buffer.
+// device list, then one DMA copy into the pinned host arena -- or, when the
+// arena has no room, a chunked copy to the heap through the pinned buffer.
 int finish_list(sieve_server *srv, Req *r) {
     uint64_t n = 0;
     int rc = compact_with(srv->view, srv->cstream, srv->view->cs, r->d_bitmap, r->lo, r->hi, r->d_list, r->list_cap,
                           &n, 1);
     if (rc) return rc;
+    bool pinned = false;
+    if (n && srv->host_arena.size) {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        pinned = srv->host_arena.alloc(n * sizeof(uint64_t), &r->harena_off);
+        if (pinned) r->harena_bytes = n * sizeof(uint64_t);
+    }
+    if (pinned) {
+        r->h_primes = reinterpret_cast<uint64_t *>(srv->host_arena.base + r->harena_off);
+        cudaError_t e = cudaMemcpyAsync(r->h_primes, r->d_list, n * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                        srv->cstream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(srv->cstream);
+        if (e != cudaSuccess) return cuda_fail(srv->view, e, "list copy");
+        r->count = n;
+        return SIEVE_OK;
+    }
     r->primes.reset(new (std::nothrow) uint64_t[n ? n : 1]);
     if (!r->primes) return SIEVE_ENOMEM;
+    r->h_primes = r->primes.get();
     for (uint64_t done = 0; done < n; done += kBounceWords) {
         const uint64_t k = std::min<uint64_t>(kBounceWords, n - done);
         cudaError_t e = cudaMemcpyAsync(srv->h_bounce, r->d_list + done, k * sizeof(uint64_t),
@@ -377,6 +400,15 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
     srv->arena.free_blocks[0] = srv->arena.size;
     e = cudaMallocHost(&srv->h_bounce, kBounceWords * sizeof(uint64_t));
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server bounce buffer"));
+    // list results go here by DMA; without it (pinning refused) they take the bounce path
+    unsigned char *ha = nullptr;
+    if (cudaMallocHost(&ha, kHostArenaBytes) == cudaSuccess) {
+        srv->host_arena.base = ha;
+        srv->host_arena.size = kHostArenaBytes;
+        srv->host_arena.free_blocks[0] = kHostArenaBytes;
+    } else {
+        cudaGetLastError();  // clear the refused allocation's error
+    }
     srv->th = std::thread(scheduler, srv.get());
     srv->finisher = std::thread(finisher, srv.get());
     *out = srv.release();
@@ -446,7 +478,7 @@ int sieve_server_poll(sieve_server *srv, uint64_t ticket, sieve_result *res, int
     res->status = r->status;
     res->kind = r->kind;
     res->count = r->count;
-    res->primes = (r->kind == SIEVE_REQ_LIST && r->status == SIEVE_OK) ? r->primes.get() : nullptr;
+    res->primes = (r->kind == SIEVE_REQ_LIST && r->status == SIEVE_OK) ? r->h_primes : nullptr;
     res->latency_us = r->latency_us;
     return SIEVE_OK;
 }
@@ -457,6 +489,7 @@ int sieve_server_release(sieve_server *srv, uint64_t ticket) {
     auto it = srv->reqs.find(ticket);
     if (it == srv->reqs.end()) return SIEVE_ENOENT;
     if (!it->second->done) return SIEVE_EBUSY;
+    if (it->second->harena_bytes) srv->host_arena.release(it->second->harena_off, it->second->harena_bytes);
     srv->reqs.erase(it);
     return SIEVE_OK;
 }
@@ -494,6 +527,8 @@ void sieve_server_destroy(sieve_server *srv) {
     }
     if (srv->arena.base) cudaFree(srv->arena.base);
     if (srv->h_bounce) cudaFreeHost(srv->h_bounce);
+    srv->reqs.clear();  // results in the host arena die with it
+    if (srv->host_arena.base) cudaFreeHost(srv->host_arena.base);
     if (srv->stream) cudaStreamDestroy(srv->stream);
     if (srv->cstream) cudaStreamDestroy(srv->cstream);
     delete srv;
