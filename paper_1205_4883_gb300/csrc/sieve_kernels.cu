@@ -266,9 +266,16 @@ __device__ __forceinline__ WheelCursor wheel_start(const WheelTables &t, uint32_
         ++Q;
     }
     const uint64_t adj = t.adj40[pc];
-    uint32_t k = 0;  // first class with c_k >= R (c_k ascends in k)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) k += (pq * c_res[j] + (uint32_t)((adj >> (5 * j)) & 31u)) < R;
+    // first class with c_k >= R: c_j = floor(p r_j / 30) < R iff p r_j < 30 R, i.e.
+    // r_j <= v = floor((30 R - 1) / p) < 30, so k = #{ j : r_j <= v }, read from
+    // nibble v of a packed table (0x...6554 holds v = 16..29)
+    uint32_t k = 0;
+    if (R) {
+        const uint64_t x = 30ull * R - 1;
+        uint64_t v = __umul64hi(x, M);
+        if (x - v * p >= p) ++v;
+        k = (uint32_t)(((v < 16 ? 0x4443322221111110ull : 0x87777776666554ull) >> (4 * (v & 15))) & 15u);
+    }
     uint64_t a = Q;
     if (k == 8) {
         k = 0;

@@ -310,3 +310,19 @@ def test_bitmap_words_from_wheel_byte_expansions():
                 e = sum(1 << ((RES[k] - 1) // 2) for k in range(8) if byte >> k & 1)
                 part |= e << (15 * j)
             assert (part >> sh) & 0xFFFFFFFF == (stream >> (32 * q)) & 0xFFFFFFFF, q
+
+
+def test_first_class_closed_form_mod30():
+    # class j's first multiple of turn a = floor(B / p) lies before wheel byte B iff
+    # c_j = floor(p r_j / 30) < R = B mod p, iff r_j <= floor((30 R - 1) / p)
+    cnt = [sum(1 for r in RES if r <= v) for v in range(30)]
+    packed = [(0x4443322221111110 >> (4 * v)) & 15 if v < 16 else (0x87777776666554 >> (4 * (v - 16))) & 15
+              for v in range(30)]
+    assert packed == cnt
+    rng = random.Random(16)
+    primes = small_primes(200000)[3:]
+    for _ in range(3000):
+        p = rng.choice(primes)
+        R = rng.randrange(0, p)
+        want = sum(1 for r in RES if p * r // 30 < R)
+        assert (cnt[(30 * R - 1) // p] if R else 0) == want, (p, R)
