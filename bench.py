@@ -525,7 +525,7 @@ def main():
     ap.add_argument("--workload", default="pi1e12", choices=["pi1e12", "batched", "served", "range2p32", "pi1e7"],
                     help="pi1e12 (default, the headline line), batched, served, range2p32 (bitmap and "
                          "u32 list of [0, 2^32)) or pi1e7 (count, bitmap and list of [0, 10^7))")
-    ap.add_argument("--rates", default="100,300,1000,3000,10000", help="served: offered loads, req/s")
+    ap.add_argument("--rates", default="100,300,1000,3000,10000,30000", help="served: offered loads, req/s")
     ap.add_argument("--requests", type=int, default=0,
                     help="served: requests per rate (0: 1 s of arrivals, between 300 and 10000)")
     args = ap.parse_args()
