@@ -10,9 +10,9 @@
 // Two ticks alternate between two sets of buffers, so the next tick is
 // already queued while the current one runs.  When a tick's event has fired,
 // its counts are added to their requests; a request whose last run is done is
-// completed; a finished list request is handed to a second host thread that
-// compacts its bitmap on its own stream and copies the primes by DMA into a
-// pinned host arena (through a pinned bounce buffer to the heap when the arena
+// completed; a finished list request is handed to one of four finisher threads,
+// which compacts its bitmap on its own stream and copies the primes by DMA into
+// a pinned host arena (through a pinned bounce buffer to the heap when the arena
 // is full), so the scheduler keeps launching ticks meanwhile.
 // Host waits poll events and condition variables; no kernel waits on anything.
 
@@ -109,6 +109,16 @@ struct Arena {
     }
 };
 
+// A host thread that completes list requests, with its own stream, compaction
+// scratch and pinned bounce buffer, so that several run side by side.
+struct Finisher {
+    cudaStream_t stream = nullptr;
+    CompactScratch cs;
+    uint64_t *bounce = nullptr;  // pinned, kBounceWords
+    std::thread th;
+};
+constexpr int kFinishers = 4;
+
 }  // namespace
 
 struct sieve_server {
@@ -116,7 +126,6 @@ struct sieve_server {
     sieve_ctx *view = nullptr;  // private context view: borrowed resident state, own buffers
     sieve_server_cfg cfg{};
     cudaStream_t stream = nullptr;   // sieve ticks
-    cudaStream_t cstream = nullptr;  // compaction of finished list requests
     Tick ticks[2];
     int next_tick = 0;
     Arena arena;
@@ -125,8 +134,7 @@ struct sieve_server {
     std::condition_variable cv_work, cv_done, cv_finish;
     std::deque<Req *> to_finish;       // list requests whose sieving is done
     bool finisher_stop = false;
-    std::thread finisher;
-    uint64_t *h_bounce = nullptr;      // pinned, kBounceWords
+    Finisher fin[kFinishers];          // compaction and copy-out of finished list requests
     Arena host_arena;                  // pinned: list results, copied in by DMA, freed on release
 
     std::map<uint64_t, std::unique_ptr<Req>> reqs;
@@ -169,16 +177,15 @@ void complete(sieve_server *srv, Req *r, int status) {
     srv->st.in_flight--;
 }
 
-constexpr size_t kBounceWords = 8u << 20;  // 64 MiB of uint64
+constexpr size_t kBounceWords = 2u << 20;  // 16 MiB of uint64 per finisher
 constexpr size_t kHostArenaBytes = 1ull << 30;  // pinned host memory for list results
 
 // Called without the lock: compaction of a finished list request into its
 // device list, then one DMA copy into the pinned host arena -- or, when the
 // arena has no room, a chunked copy to the heap through the pinned buffer.
-int finish_list(sieve_server *srv, Req *r) {
+int finish_list(sieve_server *srv, Finisher &f, Req *r) {
     uint64_t n = 0;
-    int rc = compact_with(srv->view, srv->cstream, srv->view->cs, r->d_bitmap, r->lo, r->hi, r->d_list, r->list_cap,
-                          &n, 1);
+    int rc = compact_with(srv->view, f.stream, f.cs, r->d_bitmap, r->lo, r->hi, r->d_list, r->list_cap, &n, 1);
     if (rc) return rc;
     bool pinned = false;
     if (n && srv->host_arena.size) {
@@ -189,8 +196,8 @@ int finish_list(sieve_server *srv, Req *r) {
     if (pinned) {
         r->h_primes = reinterpret_cast<uint64_t *>(srv->host_arena.base + r->harena_off);
         cudaError_t e = cudaMemcpyAsync(r->h_primes, r->d_list, n * sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                                        srv->cstream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(srv->cstream);
+                                        f.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(f.stream);
         if (e != cudaSuccess) return cuda_fail(srv->view, e, "list copy");
         r->count = n;
         return SIEVE_OK;
@@ -200,11 +207,11 @@ int finish_list(sieve_server *srv, Req *r) {
     r->h_primes = r->primes.get();
     for (uint64_t done = 0; done < n; done += kBounceWords) {
         const uint64_t k = std::min<uint64_t>(kBounceWords, n - done);
-        cudaError_t e = cudaMemcpyAsync(srv->h_bounce, r->d_list + done, k * sizeof(uint64_t),
-                                        cudaMemcpyDeviceToHost, srv->cstream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(srv->cstream);
+        cudaError_t e = cudaMemcpyAsync(f.bounce, r->d_list + done, k * sizeof(uint64_t),
+                                        cudaMemcpyDeviceToHost, f.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(f.stream);
         if (e != cudaSuccess) return cuda_fail(srv->view, e, "list copy");
-        std::memcpy(r->primes.get() + done, srv->h_bounce, k * sizeof(uint64_t));
+        std::memcpy(r->primes.get() + done, f.bounce, k * sizeof(uint64_t));
     }
     r->count = n;
     return SIEVE_OK;
@@ -236,8 +243,8 @@ void harvest(sieve_server *srv, Tick &t) {
     if (any) srv->cv_done.notify_all();
 }
 
-// Second host thread: completes list requests (compaction and copy-out).
-void finisher(sieve_server *srv) {
+// Finisher threads: complete list requests (compaction and copy-out).
+void finisher(sieve_server *srv, Finisher *f) {
     cudaSetDevice(srv->view->device);
     std::unique_lock<std::mutex> lk(srv->mu);
     for (;;) {
@@ -246,7 +253,7 @@ void finisher(sieve_server *srv) {
         Req *r = srv->to_finish.front();
         srv->to_finish.pop_front();
         lk.unlock();
-        const int rc = finish_list(srv, r);
+        const int rc = finish_list(srv, *f, r);
         lk.lock();
         srv->arena.release(r->arena_off, r->arena_bytes);
         srv->st.device_bytes_reserved = srv->arena.used;
@@ -383,7 +390,8 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
     };
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&srv->cstream, cudaStreamNonBlocking);
+    for (Finisher &f : srv->fin)
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server streams"));
     v->stream = srv->stream;
     for (Tick &t : srv->ticks) {
@@ -398,8 +406,10 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server arena"));
     srv->arena.size = srv->cfg.max_device_bytes;
     srv->arena.free_blocks[0] = srv->arena.size;
-    e = cudaMallocHost(&srv->h_bounce, kBounceWords * sizeof(uint64_t));
-    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server bounce buffer"));
+    for (Finisher &f : srv->fin) {
+        e = cudaMallocHost(&f.bounce, kBounceWords * sizeof(uint64_t));
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server bounce buffer"));
+    }
     // list results go here by DMA; without it (pinning refused) they take the bounce path
     unsigned char *ha = nullptr;
     if (cudaMallocHost(&ha, kHostArenaBytes) == cudaSuccess) {
@@ -410,7 +420,7 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
         cudaGetLastError();  // clear the refused allocation's error
     }
     srv->th = std::thread(scheduler, srv.get());
-    srv->finisher = std::thread(finisher, srv.get());
+    for (Finisher &f : srv->fin) f.th = std::thread(finisher, srv.get(), &f);
     *out = srv.release();
     return SIEVE_OK;
 }
@@ -514,7 +524,8 @@ void sieve_server_destroy(sieve_server *srv) {
         srv->finisher_stop = true;
     }
     srv->cv_finish.notify_all();
-    if (srv->finisher.joinable()) srv->finisher.join();
+    for (Finisher &f : srv->fin)
+        if (f.th.joinable()) f.th.join();
     if (srv->view) {
         cudaSetDevice(srv->view->device);
         if (srv->stream) cudaStreamSynchronize(srv->stream);
@@ -522,15 +533,18 @@ void sieve_server_destroy(sieve_server *srv) {
             for (auto &lb : t.lb) free_launch_buffers(srv->view, lb);
             if (t.ev) cudaEventDestroy(t.ev);
         }
+        for (Finisher &f : srv->fin) free_compact_scratch(srv->view, f.cs);
         srv->view->stream = nullptr;  // the view does not own the stream
         sieve_destroy(srv->view);
     }
     if (srv->arena.base) cudaFree(srv->arena.base);
-    if (srv->h_bounce) cudaFreeHost(srv->h_bounce);
+    for (Finisher &f : srv->fin) {
+        if (f.bounce) cudaFreeHost(f.bounce);
+        if (f.stream) cudaStreamDestroy(f.stream);
+    }
     srv->reqs.clear();  // results in the host arena die with it
     if (srv->host_arena.base) cudaFreeHost(srv->host_arena.base);
     if (srv->stream) cudaStreamDestroy(srv->stream);
-    if (srv->cstream) cudaStreamDestroy(srv->cstream);
     delete srv;
 }
 
