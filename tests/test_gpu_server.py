@@ -104,3 +104,26 @@ def test_admission_and_errors(sv):
         with gb.Server(sv) as srv2:
             gb.sieve_server_poll(srv2.srv, 12345, 0)
     assert e.value.code == gb.SIEVE_ENOENT
+
+
+def test_list_results_beyond_the_pinned_arena(sv):
+    # four list results of ~48M primes (~385 MB each) held at once: the first ones land in
+    # the 1 GiB pinned arena, the last one on the heap (bounce-buffer path); all exact
+    ranges = [(10**9 * k, 10**9 * (k + 1)) for k in range(1, 5)]
+    with gb.Server(sv, max_device_bytes=6 << 30) as srv:
+        tickets = []
+        for lo, hi in ranges:
+            rc, t = srv.submit(lo, hi, gb.SIEVE_REQ_LIST)
+            assert rc == gb.SIEVE_OK
+            tickets.append(t)
+        results = []
+        for t in tickets:
+            rc, res = srv.poll(t, timeout_us=120_000_000)
+            assert rc == gb.SIEVE_OK and res["status"] == gb.SIEVE_OK
+            results.append(res)
+        for (lo, hi), res in zip(ranges, results):
+            want = sv.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)
+            assert res["count"] == len(want) == oracle.count(lo, hi)
+            assert np.array_equal(res["primes"], want), (lo, hi)
+        for t in tickets:
+            assert srv.release(t) == gb.SIEVE_OK
