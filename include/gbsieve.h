@@ -264,7 +264,9 @@ void sieve_server_destroy(sieve_server *srv);
                                         heaviest and lightest alternating (2); results are the same */
 #define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
                                        primes, carried across the segments of a work item; used
-                                       when they fit (default 64; 0 = recompute per segment) */
+                                       when they fit and enough segments resume one (half of a
+                                       single range's, three quarters of a batch's) (default
+                                       1024; 0 = recompute per segment) */
 
 /* Set a launch parameter for later calls on ctx (SIEVE_EINVAL if out of range). */
 int sieve_set_param(sieve_ctx *ctx, int param, int64_t value);

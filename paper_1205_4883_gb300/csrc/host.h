@@ -21,7 +21,7 @@ struct Params {
     int ctas_per_sm = 1;
     uint32_t chunk_segs = 16;
     uint64_t bucket_limit = 1ull << 62;  // primes >= this use the bucket lists; 0: the segment size
-    uint32_t cursor_mb = 64;             // budget for per-CTA large-prime cursors (0: recompute every segment)
+    uint32_t cursor_mb = 1024;           // budget for per-CTA large-prime cursors (0: recompute every segment)
     uint32_t mr_percent = 0;             // Miller-Rabin path when width < this % of the skipped primes (0: off)
     int wheel = 30;                      // count-only launches on the mod-30 or the mod-210 wheel
     uint32_t small_limit210 = 128;       // mod-210: primes below this are crossed warp-cooperatively

@@ -163,6 +163,19 @@ void free_compact_scratch(sieve_ctx *ctx, CompactScratch &cs) {
 
 // Fill one RangeDesc (item_first is set at launch).  Segments start at a wheel
 // byte Bbase with 30 Bbase <= lo and 30 Bbase + 1 = (lo | 1) (mod 64).
+// Whether per-CTA cursors pay for themselves with chunks of C segments: they
+// save the start computation of every large prime in every segment of a chunk
+// but its first, and cost their stores and coarser work items.  Measured: a
+// single range gains from half its segments resuming (at 10^14: 18 % with half,
+// 35 % with 94 %); a batch of mostly one-segment ranges loses (9 % with 49 %),
+// so batches need three quarters.
+bool cursors_pay(const RangeDesc *rd, size_t m, uint32_t C, uint64_t segs) {
+    if (C < 2 || segs == 0) return false;
+    uint64_t resumes = 0;
+    for (size_t i = 0; i < m; ++i) resumes += rd[i].nseg - (rd[i].nseg + C - 1) / C;
+    return m == 1 ? 2 * resumes >= segs : 4 * resumes >= 3 * segs;
+}
+
 RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_bytes, int mode,
                      uint32_t *bitmap) {
     RangeDesc r;
@@ -211,15 +224,14 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
     // Per-CTA cursors for the large primes (4 B each) when they fit the budget
     // and every offset fits 29 bits (p < 2^27); not with bucket lists.
     const uint32_t n_large = nmax > mid_end ? nmax - mid_end : 0;
-    const bool cursors = cs && !buckets && n_large && h[nmax - 1] < (1u << 27) &&
-                         (uint64_t)grid * n_large * 4 <= (uint64_t)prm.cursor_mb << 20;
+    bool cursors = cs && !buckets && n_large && h[nmax - 1] < (1u << 27) &&
+                   (uint64_t)grid * n_large * 4 <= (uint64_t)prm.cursor_mb << 20;
     // Chunks (several segments per work item) pay off with bucket lists and
     // cursors; keep at least 4 items per CTA so the last wave stays short.
-    uint32_t C = 1;
-    if (buckets || cursors) {
-        C = prm.chunk_segs;
-        while (C > 1 && segs / C < 4 * grid) C /= 2;
-    }
+    uint32_t C = prm.chunk_segs;
+    while (C > 1 && segs / C < 4 * grid) C /= 2;
+    if (cursors && !cursors_pay(rd, m, C, segs)) cursors = false;
+    if (!buckets && !cursors) C = 1;
     uint64_t items = 0;
     for (size_t i = 0; i < m; ++i) {
         rd[i].item_first = items;
@@ -388,13 +400,12 @@ int prepare_launch210(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size
     const uint32_t mid_lim = prm.mid_limit210 ? prm.mid_limit210 : std::max<uint32_t>(sw / 6, 23);
     const uint32_t mid_end = std::max(small_end, first_at_least(h, mid_lim));
     const uint32_t n_large = nmax > mid_end ? nmax - mid_end : 0;
-    const bool cursors = cs && n_large && h[nmax - 1] < (1u << 27) &&
-                         (uint64_t)grid * n_large * 4 <= (uint64_t)prm.cursor_mb << 20;
-    uint32_t C = 1;
-    if (cursors) {
-        C = prm.chunk_segs;
-        while (C > 1 && segs / C < 4 * grid) C /= 2;
-    }
+    bool cursors = cs && n_large && h[nmax - 1] < (1u << 27) &&
+                   (uint64_t)grid * n_large * 4 <= (uint64_t)prm.cursor_mb << 20;
+    uint32_t C = prm.chunk_segs;
+    while (C > 1 && segs / C < 4 * grid) C /= 2;
+    if (cursors && !cursors_pay(rd, m, C, segs)) cursors = false;
+    if (!cursors) C = 1;
     uint64_t items = 0;
     for (size_t i = 0; i < m; ++i) {
         rd[i].item_first = items;
