@@ -306,7 +306,8 @@ void *sieve_stream(sieve_ctx *ctx);
 /* Static name of an error code. */
 const char *sieve_strerror(int code);
 
-/* The context's last error message ("" if none); valid until the next call. */
+/* The context's last error message ("" if none): a buffer of the context,
+ * overwritten by the next failure on it (or on a server started from it). */
 const char *sieve_last_error(sieve_ctx *ctx);
 
 #ifdef __cplusplus

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -116,7 +117,9 @@ struct sieve_ctx {
 
     std::atomic<uint64_t> device_bytes{0};
     bool shadow = false;  // a server's private view: resident arrays are borrowed, not owned
-    std::string last_error;
+    // the last failure's message; server threads share a view, so writes are serialised
+    std::mutex err_mu;
+    char last_error[256] = {0};
 };
 
 namespace gbs {

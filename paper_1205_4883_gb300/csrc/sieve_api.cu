@@ -34,7 +34,10 @@ const char *kNames[] = {"ok", "invalid argument", "range exceeds limit", "output
 }  // namespace
 
 int fail(sieve_ctx *c, int code, const std::string &msg) {
-    if (c) c->last_error = msg;
+    if (c) {
+        std::lock_guard<std::mutex> lk(c->err_mu);
+        std::snprintf(c->last_error, sizeof c->last_error, "%s", msg.c_str());
+    }
     return code;
 }
 
@@ -712,7 +715,7 @@ const char *sieve_strerror(int code) {
     return kNames[i];
 }
 
-const char *sieve_last_error(sieve_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+const char *sieve_last_error(sieve_ctx *ctx) { return ctx ? ctx->last_error : ""; }
 
 uint64_t sieve_bitmap_words(uint64_t lo, uint64_t hi) { return lo > hi ? 0 : bitmap_words_of(lo, hi); }
 
