@@ -307,7 +307,7 @@ void *sieve_stream(sieve_ctx *ctx);
 const char *sieve_strerror(int code);
 
 /* The context's last error message ("" if none): a buffer of the context,
- * overwritten by the next failure on it (or on a server started from it). */
+ * overwritten by its next failure. */
 const char *sieve_last_error(sieve_ctx *ctx);
 
 #ifdef __cplusplus
