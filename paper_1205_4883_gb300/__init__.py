@@ -242,16 +242,20 @@ def sieve_compact_static(bitmap, lo: int, hi: int, out, cap: Optional[int] = Non
 
 def sieve_batch_count(ctx: int, lo: Sequence[int], hi: Sequence[int], bitmaps=None):
     """Counts of m ranges in one launch; `bitmaps` optionally a list of CUDA tensors (or None)."""
+    import numpy as np
     m = len(lo)
     if len(hi) != m:
         raise ValueError("lo and hi differ in length")
-    LoArr = _u64 * max(m, 1)
-    lo_a, hi_a, cnt = LoArr(*lo), LoArr(*hi), LoArr()
+    # contiguous uint64 arrays passed by pointer (no per-element ctypes conversion)
+    lo_a = np.ascontiguousarray(lo, dtype=np.uint64) if m else np.zeros(1, np.uint64)
+    hi_a = np.ascontiguousarray(hi, dtype=np.uint64) if m else np.zeros(1, np.uint64)
+    cnt = np.zeros(max(m, 1), dtype=np.uint64)
     bm = None
     if bitmaps is not None:
         bm = (_vp * max(m, 1))(*[(_ptr(b) or None) for b in bitmaps])
-    _check(ctx, load_library().sieve_batch_count(ctx, lo_a, hi_a, m, cnt, bm))
-    return [int(cnt[i]) for i in range(m)]
+    as_u64 = lambda a: a.ctypes.data_as(_pu64)  # noqa: E731
+    _check(ctx, load_library().sieve_batch_count(ctx, as_u64(lo_a), as_u64(hi_a), m, as_u64(cnt), bm))
+    return cnt[:m].tolist()
 
 
 def sieve_set_param(ctx: int, param: int, value: int) -> None:

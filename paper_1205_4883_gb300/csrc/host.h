@@ -94,6 +94,7 @@ struct sieve_ctx {
     uint32_t *d_primes = nullptr;
     uint64_t *d_magic = nullptr;
     std::vector<uint32_t> h_primes;
+    std::vector<uint32_t> h_prime_bucket;  // [b]: index of the first base prime >= 1024 b
     uint8_t *d_tile = nullptr;
     uint64_t tile_stride = 0;
     // the same for the mod-210 count path: pattern of 11..19 and the class tables
@@ -128,7 +129,7 @@ int fail(sieve_ctx *c, int code, const std::string &msg);
 int cuda_fail(sieve_ctx *c, cudaError_t e, const char *where);
 uint64_t isqrt64(uint64_t n);
 uint64_t bitmap_words_of(uint64_t lo, uint64_t hi);
-RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_bytes, int mode,
+RangeDesc plan_range(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t seg_bytes, int mode,
                      uint32_t *bitmap);
 int alloc_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb, size_t m);
 void free_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb);
@@ -138,7 +139,7 @@ void free_compact_scratch(sieve_ctx *ctx, CompactScratch &cs);
 // Sieve the m ranges lb.h_ranges()[0..m) (planned with plan_range) on
 // `stream`: fills in the launch header, copies the block, clears the
 // accumulators and launches.  Bucket lists are used only if `bs` is given.
-RangeDesc plan_range210(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_words);
+RangeDesc plan_range210(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t seg_words);
 uint32_t w210_segment_words(const Params &prm);
 int launch_ranges210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, LaunchBuffers &lb, size_t m,
                      CursorStore *cs);

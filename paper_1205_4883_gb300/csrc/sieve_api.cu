@@ -9,6 +9,7 @@
 // 65536.  Every round's output is a list made by the compaction kernels.
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -48,18 +49,14 @@ int cuda_fail(sieve_ctx *c, cudaError_t e, const char *where) {
     return fail(c, SIEVE_ECUDA, m);
 }
 
+// floor(sqrt(n)) for n < 2^64: the double square root is within one of it,
+// then exact integer corrections (r < 2^32, so (r + 1)^2 does not overflow
+// below 2^64 - 2^33).
 uint64_t isqrt64(uint64_t n) {
-    uint64_t r = 0, bit = 1ull << 62;
-    while (bit > n) bit >>= 2;
-    while (bit) {
-        if (n >= r + bit) {
-            n -= r + bit;
-            r = (r >> 1) + bit;
-        } else {
-            r >>= 1;
-        }
-        bit >>= 2;
-    }
+    uint64_t r = (uint64_t)std::sqrt((double)n);
+    if (r > 0xffffffffull) r = 0xffffffffull;
+    while (r * r > n) --r;
+    while (r < 0xffffffffull && (r + 1) * (r + 1) <= n) ++r;
     return r;
 }
 
@@ -73,11 +70,25 @@ uint64_t bitmap_words_of(uint64_t lo, uint64_t hi) {
 namespace {
 
 // Number of base primes p with p * p < hi, i.e. p <= floor(sqrt(hi - 1)).
-uint32_t primes_needed(const std::vector<uint32_t> &primes, uint64_t hi) {
+// Base primes p <= sqrt(hi - 1): a binary search inside the bucket of 1024
+// integers that holds the bound (ctx->h_prime_bucket[b] = index of the first
+// base prime >= 1024 b).
+uint32_t primes_needed(const sieve_ctx *ctx, uint64_t hi) {
     if (hi < 2) return 0;
-    uint64_t lim = isqrt64(hi - 1);
-    return (uint32_t)(std::upper_bound(primes.begin(), primes.end(), lim,
-                                       [](uint64_t v, uint32_t p) { return v < p; }) -
+    const std::vector<uint32_t> &primes = ctx->h_primes;
+    const std::vector<uint32_t> &bucket = ctx->h_prime_bucket;
+    const uint64_t lim = isqrt64(hi - 1);
+    auto first = primes.begin(), last = primes.end();
+    if (!bucket.empty()) {
+        const uint64_t b = lim / 1024;
+        if (b + 1 < bucket.size()) {
+            first = primes.begin() + bucket[b];
+            last = primes.begin() + bucket[b + 1];
+        } else {
+            first = primes.begin() + bucket.back();
+        }
+    }
+    return (uint32_t)(std::upper_bound(first, last, lim, [](uint64_t v, uint32_t p) { return v < p; }) -
                       primes.begin());
 }
 
@@ -179,7 +190,7 @@ bool cursors_pay(const RangeDesc *rd, size_t m, uint32_t C, uint64_t segs) {
     return m == 1 ? 2 * resumes >= segs : 4 * resumes >= 3 * segs;
 }
 
-RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_bytes, int mode,
+RangeDesc plan_range(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t seg_bytes, int mode,
                      uint32_t *bitmap) {
     RangeDesc r;
     std::memset(&r, 0, sizeof r);
@@ -199,7 +210,7 @@ RangeDesc plan_range(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t 
     r.Bbase = t0 / 30;
     const uint64_t span = 30ull * seg_bytes;
     r.nseg = (uint64_t)(((int64_t)hi - t0 + (int64_t)span - 1) / (int64_t)span);
-    r.n_use = primes_needed(primes, hi);
+    r.n_use = primes_needed(ctx, hi);
     uint64_t corr = (lo <= 2 && 2 < hi) ? 1 : 0;
     if (mode == kModeCount) corr += (lo <= 3 && 3 < hi ? 1 : 0) + (lo <= 5 && 5 < hi ? 1 : 0);
     r.corr = corr;
@@ -369,7 +380,7 @@ uint32_t w210_segment_words(const Params &prm) {
 }
 
 // One range on the mod-210 wheel: segments start at group lo / 210.
-RangeDesc plan_range210(const std::vector<uint32_t> &primes, uint64_t lo, uint64_t hi, uint32_t seg_words) {
+RangeDesc plan_range210(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t seg_words) {
     RangeDesc r;
     std::memset(&r, 0, sizeof r);
     r.lo = lo;
@@ -378,7 +389,7 @@ RangeDesc plan_range210(const std::vector<uint32_t> &primes, uint64_t lo, uint64
     r.Bbase = (int64_t)(lo / 210);
     const uint64_t span = 210ull * (seg_words / 3 * 2);
     r.nseg = (hi - 210ull * (uint64_t)r.Bbase + span - 1) / span;
-    r.n_use = primes_needed(primes, hi);
+    r.n_use = primes_needed(ctx, hi);
     for (uint64_t q : {2, 3, 5, 7}) r.corr += lo <= q && q < hi;
     return r;
 }
@@ -563,7 +574,7 @@ int primes_upto(sieve_ctx *ctx, uint64_t limit, uint32_t **out_dev, std::vector<
     if (rc) return rc;
     rc = ensure_bitmap(ctx, bitmap_words_of(0, hi));
     if (rc) return rc;
-    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, 0, hi, ctx->params.seg_bytes, kModeBitmap, ctx->d_bitmap);
+    ctx->lb.h_ranges()[0] = plan_range(ctx, 0, hi, ctx->params.seg_bytes, kModeBitmap, ctx->d_bitmap);
     rc = run_sync(ctx, ctx->params, kModeBitmap, 1);
     if (rc) return rc;
     uint64_t n = 0;
@@ -627,6 +638,12 @@ int make_base_primes(sieve_ctx *ctx) {
     std::vector<uint32_t> &h = ctx->h_primes;
     h.resize(std::upper_bound(h.begin(), h.end(), (uint32_t)std::min<uint64_t>(ctx->prime_limit, 0xffffffffu)) -
              h.begin());
+    std::vector<uint32_t> &bucket = ctx->h_prime_bucket;
+    bucket.assign(ctx->prime_limit / 1024 + 2, 0);
+    for (size_t b = 0, i = 0; b < bucket.size(); ++b) {
+        while (i < h.size() && h[i] < 1024ull * b) ++i;
+        bucket[b] = (uint32_t)i;
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return SIEVE_OK;
 }
@@ -647,7 +664,7 @@ int bitmap_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, uin
     int rc = ensure_launch(ctx, 1);
     if (rc) return rc;
     const Params prm = single_range_params(ctx, lo, hi);
-    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, prm.seg_bytes, kModeBitmap, out_dev);
+    ctx->lb.h_ranges()[0] = plan_range(ctx, lo, hi, prm.seg_bytes, kModeBitmap, out_dev);
     rc = run_sync(ctx, prm, kModeBitmap, 1);
     if (rc) return rc;
     if (count) *count = ctx->lb.h_acc[0];
@@ -814,7 +831,7 @@ int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count) {
     rc = ensure_launch(ctx, 1);
     if (rc) return rc;
     if (ctx->params.wheel == 210) {
-        ctx->lb.h_ranges()[0] = plan_range210(ctx->h_primes, lo, hi, w210_segment_words(ctx->params));
+        ctx->lb.h_ranges()[0] = plan_range210(ctx, lo, hi, w210_segment_words(ctx->params));
         rc = launch_ranges210(ctx, ctx->stream, ctx->params, ctx->lb, 1, &ctx->cursors);
         int of = 0;
         if (!rc) rc = finish(ctx, ctx->lb, 1, &of);
@@ -823,7 +840,7 @@ int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count) {
         return SIEVE_OK;
     }
     const Params prm = single_range_params(ctx, lo, hi);
-    ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, prm.seg_bytes, kModeCount, nullptr);
+    ctx->lb.h_ranges()[0] = plan_range(ctx, lo, hi, prm.seg_bytes, kModeCount, nullptr);
     rc = run_sync(ctx, prm, kModeCount, 1);
     if (rc) return rc;
     *count = ctx->lb.h_acc[0];
@@ -838,11 +855,11 @@ int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_de
     rc = ensure_launch(ctx, 1);
     if (rc) return rc;
     if (ctx->params.wheel == 210) {
-        ctx->lb.h_ranges()[0] = plan_range210(ctx->h_primes, lo, hi, w210_segment_words(ctx->params));
+        ctx->lb.h_ranges()[0] = plan_range210(ctx, lo, hi, w210_segment_words(ctx->params));
         rc = launch_ranges210(ctx, ctx->stream, ctx->params, ctx->lb, 1, &ctx->cursors);
     } else {
         const Params prm = single_range_params(ctx, lo, hi);
-        ctx->lb.h_ranges()[0] = plan_range(ctx->h_primes, lo, hi, prm.seg_bytes, kModeCount, nullptr);
+        ctx->lb.h_ranges()[0] = plan_range(ctx, lo, hi, prm.seg_bytes, kModeCount, nullptr);
         rc = launch_ranges(ctx, ctx->stream, prm, kModeCount, ctx->lb, 1, &ctx->buckets, &ctx->cursors);
     }
     if (rc) return rc;
@@ -917,8 +934,8 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, si
     if (rc) return rc;
     const int mode = bitmaps_dev ? kModeBitmap : ctx->params.wheel == 210 ? kModeCount210 : kModeCount;
     auto plan = [&](size_t i) {
-        return mode == kModeCount210 ? plan_range210(ctx->h_primes, lo[i], hi[i], w210_segment_words(ctx->params))
-                                     : plan_range(ctx->h_primes, lo[i], hi[i], ctx->params.seg_bytes, mode,
+        return mode == kModeCount210 ? plan_range210(ctx, lo[i], hi[i], w210_segment_words(ctx->params))
+                                     : plan_range(ctx, lo[i], hi[i], ctx->params.seg_bytes, mode,
                                                   bitmaps_dev ? bitmaps_dev[i] : nullptr);
     };
     // Launch order (SIEVE_PARAM_BATCH_ORDER): as given, heaviest first, or heaviest
@@ -1073,7 +1090,7 @@ int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clea
         return (x / W) * cum[W] + cum[x % W];
     };
     uint64_t total = 0;
-    const uint32_t n_use = primes_needed(ctx->h_primes, hi);
+    const uint32_t n_use = primes_needed(ctx, hi);
     for (uint32_t i = kFirstCrossingPrime; i < n_use; ++i) {
         const uint64_t p = ctx->h_primes[i];
         uint64_t m_lo = std::max<uint64_t>(p, (lo + p - 1) / p);

@@ -164,7 +164,7 @@ RangeDesc plan_run(sieve_server *srv, const Req &r, uint64_t a, uint64_t b, int 
     const uint64_t hi = b == r.plan.nseg ? r.hi : (uint64_t)(30 * r.plan.Bbase) + b * span;
     uint32_t *bm = nullptr;
     if (mode == kModeBitmap) bm = r.d_bitmap + ((lo | 1) - (r.lo | 1)) / 64;
-    return plan_range(srv->view->h_primes, lo, hi, srv->view->params.seg_bytes, mode, bm);
+    return plan_range(srv->view, lo, hi, srv->view->params.seg_bytes, mode, bm);
 }
 
 // Mark an admitted request finished (lock held); it leaves the in-flight count.
@@ -381,6 +381,7 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
     v->d_primes = ctx->d_primes;
     v->d_magic = ctx->d_magic;
     v->h_primes = ctx->h_primes;
+    v->h_prime_bucket = ctx->h_prime_bucket;
     v->d_tile = ctx->d_tile;
     v->tile_stride = ctx->tile_stride;
     v->params = ctx->params;
@@ -436,7 +437,7 @@ int sieve_server_submit(sieve_server *srv, const sieve_req *req, uint64_t *ticke
     r->kind = req->kind;
     r->t_submit = Clock::now();
     const int mode = r->kind == SIEVE_REQ_LIST ? kModeBitmap : kModeCount;
-    r->plan = plan_range(srv->view->h_primes, r->lo, r->hi, srv->view->params.seg_bytes, mode, nullptr);
+    r->plan = plan_range(srv->view, r->lo, r->hi, srv->view->params.seg_bytes, mode, nullptr);
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) return SIEVE_EINVAL;
     if (srv->reqs.size() >= srv->cfg.max_requests) {
