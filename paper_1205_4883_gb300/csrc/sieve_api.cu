@@ -506,13 +506,15 @@ int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const 
 
 namespace {
 
-// Copy the m counts and the overflow flag to lb.h_acc and wait; *overflowed = 1
-// if a bucket list overflowed (the results are then invalid).
+// Copy the m counts and the flag word to lb.h_acc and wait; *overflowed = 1 if
+// a bucket list overflowed (bit 0: the results are then invalid, a retry with
+// larger lists helps); bit 1 is a wait that hit its limit in the kernel.
 int finish(sieve_ctx *ctx, LaunchBuffers &lb, size_t m, int *overflowed) {
     CK(cudaMemcpyAsync(lb.h_acc, lb.d_acc + 1, (m + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    *overflowed = (lb.h_acc[m] & 0xffffffffull) != 0;
+    if (lb.h_acc[m] & 2ull) return fail(ctx, SIEVE_EDEVICE, "a device-side wait hit its limit");
+    *overflowed = (lb.h_acc[m] & 1ull) != 0;
     return SIEVE_OK;
 }
 

@@ -9,7 +9,7 @@
 // r = {1, 7, 11, 13, 17, 19, 23, 29}.  Per segment a CTA
 //   1. copies the pre-sieved pattern (multiples of 7, 11, 13, 17, 19 already
 //      cleared; period 323323 bytes) from one of 16 byte-shifted copies held
-//      in L2, so every copy is 16-byte aligned;
+//      in L2, so every copy is 16-byte aligned, with one cp.async.bulk;
 //   2. crosses off, for every base prime p >= 23 and every wheel class j, the
 //      arithmetic progression of multiples p m with m = r_j (mod 30), m >= p:
 //      in wheel bytes it is c_j + p q (c_j = floor(p r_j / 30)) with a fixed
@@ -307,6 +307,42 @@ __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v, int lane) {
     return v;
 }
 
+// Bulk (TMA) copy of the pattern tile into shared memory, completed on an
+// mbarrier: one thread arms the barrier with the byte count and issues one
+// cp.async.bulk global -> shared; every thread waits on the barrier's phase.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Orders this thread's earlier shared-memory accesses (and, after a barrier,
+// the block's) before its later async-proxy operations on shared memory.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Polls before a wait is declared failed (each try_wait may itself suspend the
+// thread for a while): far beyond any copy of a few hundred KB from L2.
+constexpr uint32_t kWaitLimit = 1u << 24;
+
 template <int MODE>
 __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict__ Pg) {
     extern __shared__ uint4 smem4[];
@@ -323,6 +359,14 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
     __shared__ uint32_t s_nseg;                     // base primes with p^2 below the segment end
     __shared__ uint32_t s_nbucket;                  // bucket primes with p^2 below the chunk end
     __shared__ uint32_t s_cnt[kMaxChunkSegments];  // bucket fill counts, one per segment of the chunk
+    __shared__ __align__(8) uint64_t s_tile_bar;    // completes the pattern copy of each segment
+    __shared__ uint32_t s_tile_fail;                // a wait for it hit kWaitLimit: the CTA stops
+    uint32_t tile_phase = 0;
+    if (threadIdx.x == 0) {
+        s_tile_fail = 0;
+        mbar_init(&s_tile_bar, 1);
+        fence_proxy_async_smem();
+    }
 
     init_tables(tab);
     const int tid = threadIdx.x, lane = tid & 31;
@@ -422,13 +466,20 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             const int64_t hi_rel = (int64_t)rd.hi - base_int, lo_rel = (int64_t)rd.lo - base_int;
             const uint32_t L = chunk_bytes - g * S < S ? chunk_bytes - g * S : S;
 
-            // 1. pre-sieved pattern -> shared memory (16-byte aligned copy)
+            // 1. pre-sieved pattern -> shared memory: one bulk (TMA) copy of the
+            //    16-byte aligned shifted tile, overlapped with the prime-bound
+            //    search below and waited for before the crossing starts
             {
                 int64_t ph = B0 % (int64_t)kTilePeriod;
                 if (ph < 0) ph += kTilePeriod;
                 const uint32_t k = (uint32_t)ph & 15u;
                 const uint4 *src = reinterpret_cast<const uint4 *>(P.tile + k * P.tile_stride + ((uint32_t)ph - k));
-                for (uint32_t i = tid; i < L / 16; i += blockDim.x) smem4[i] = __ldg(src + i);
+                // the previous segment's accesses are ordered before the copy by
+                // the barrier that ended it and this fence
+                if (tid == 0) {
+                    fence_proxy_async_smem();
+                    bulk_copy_g2s(smem4, src, L, &s_tile_bar);
+                }
             }
             // primes with p^2 >= the segment's end have no multiple to cross here
             if (tid < 32) {
@@ -447,7 +498,15 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                     s_R[t] = mod_barrett(Bc, __ldg(P.primes + kFirstCrossingPrime + t),
                                          __ldg(P.magic + kFirstCrossingPrime + t));
             }
+            {
+                uint32_t tries = 0;
+                while (!mbar_try_wait(&s_tile_bar, tile_phase) && ++tries < kWaitLimit) {
+                }
+                if (tries >= kWaitLimit) s_tile_fail = 1;
+                tile_phase ^= 1u;
+            }
             __syncthreads();
+            if (s_tile_fail) break;  // every thread sees it after the barrier
             // a range on the Miller-Rabin path is sieved with the primes below 2^16 only
             const uint32_t n_seg = rd.mr && P.mr_end < s_nseg ? P.mr_end : s_nseg;
             // primes crossed here (not through the buckets): [8, n_use)
@@ -647,6 +706,10 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             }
             n_prev = n_use;
             __syncthreads();
+        }
+        if (s_tile_fail) {  // reported to the host as a device error; the CTA stops here
+            if (tid == 0) atomicOr(P.overflow, 2u);
+            break;
         }
     }
 }
