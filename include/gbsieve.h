@@ -262,6 +262,9 @@ void sieve_server_destroy(sieve_server *srv);
 #define SIEVE_PARAM_BATCH_ORDER   13 /* sieve_batch_count launches the ranges in the given order
                                         (0, default), heaviest first by estimated work (1), or
                                         heaviest and lightest alternating (2); results are the same */
+#define SIEVE_PARAM_FAULT_WAIT    14 /* test hook: 1 = synchronous calls report the failure of a
+                                        device-side wait (SIEVE_EDEVICE) after their launch, as the
+                                        sieve does when a bounded wait in a kernel runs out */
 #define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
                                        primes, carried across the segments of a work item; used
                                        when they fit and enough segments resume one (half of a
@@ -290,6 +293,15 @@ int sieve_get_info(sieve_ctx *ctx, sieve_info *info);
  * host array out[0 .. min(cap, n)); *n receives their number.
  */
 int sieve_base_primes(sieve_ctx *ctx, uint32_t *out, size_t cap, uint64_t *n);
+
+/*
+ * Self-test of the bounded device-side wait the sieve uses for its bulk
+ * shared-memory copies: one CTA waits on an mbarrier for at most `limit` polls.
+ * With arm != 0 a 4 KB bulk copy completes the barrier (*timed_out = 0); with
+ * arm == 0 nothing does, the wait runs out and *timed_out = 1 -- the kernel
+ * returns normally and the context stays usable.  SIEVE_EINVAL for limit 0.
+ */
+int sieve_selftest_wait(sieve_ctx *ctx, int arm, uint32_t limit, int *timed_out);
 
 /*
  * Exact number of bit-clears the crossing-off loop performs for [lo, hi):

@@ -39,6 +39,7 @@ SIEVE_PARAM_WHEEL = 10
 SIEVE_PARAM_SMALL_LIMIT_210 = 11
 SIEVE_PARAM_MID_LIMIT_210 = 12
 SIEVE_PARAM_BATCH_ORDER = 13
+SIEVE_PARAM_FAULT_WAIT = 14
 
 _u64 = ctypes.c_uint64
 _i64 = ctypes.c_int64
@@ -104,6 +105,7 @@ _SIGS = {
     "sieve_server_release": (_int, [_vp, _u64]),
     "sieve_server_stats": (_int, [_vp, ctypes.POINTER(sieve_server_counters)]),
     "sieve_server_destroy": (None, [_vp]),
+    "sieve_selftest_wait": (_int, [_vp, _int, ctypes.c_uint32, ctypes.POINTER(_int)]),
 }
 
 _lib = None
@@ -238,6 +240,13 @@ def sieve_compact_static(bitmap, lo: int, hi: int, out, cap: Optional[int] = Non
     rc = load_library().sieve_compact_static(_ptr(bitmap), lo, hi, _ptr(out), cap, ctypes.byref(n), stream or None)
     _check(0, rc, allow=(SIEVE_ETRUNC,))
     return n.value, rc
+
+
+def sieve_selftest_wait(ctx: int, arm: bool, limit: int) -> bool:
+    """Run the bounded device-wait self-test; True if the wait ran out."""
+    out = _int()
+    _check(ctx, load_library().sieve_selftest_wait(ctx, 1 if arm else 0, limit, ctypes.byref(out)))
+    return bool(out.value)
 
 
 def sieve_batch_count(ctx: int, lo: Sequence[int], hi: Sequence[int], bitmaps=None):

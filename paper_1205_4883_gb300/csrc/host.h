@@ -28,6 +28,7 @@ struct Params {
     uint32_t small_limit210 = 128;       // mod-210: primes below this are crossed warp-cooperatively
     uint32_t mid_limit210 = 0;           // mod-210: primes below this use per-class sub-progressions; 0: words / 6
     int batch_order = 0;                 // batches: 0 as given, 1 heaviest first, 2 heaviest/lightest alternating
+    int fault_wait = 0;                  // test hook: synchronous launches report a device-wait failure
 };
 
 // Everything one sieve launch reads and writes besides the resident state:

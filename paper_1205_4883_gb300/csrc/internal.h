@@ -121,6 +121,11 @@ cudaError_t launch_sieve210(const SieveLaunch *d_launch, const W210Tables *tab, 
 cudaError_t launch_build_tile210(const W210Tables *tab, uint8_t *tile, uint64_t stride, uint32_t len,
                                  cudaStream_t stream);
 
+// Self-test of the bounded mbarrier wait used by the sieve's bulk copies
+// (sieve_kernels.cu): *status_dev = 0 if the wait completed, 1 if it hit `limit`.
+cudaError_t launch_wait_selftest(const void *src, uint32_t bytes, int arm, uint32_t limit, int *status_dev,
+                                 cudaStream_t stream);
+
 // Compaction of an odd-only bitmap into a prime list.
 constexpr uint32_t kCompactTileWords = 2048;  // 256 threads x 8 words
 cudaError_t launch_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *tile_counts,

@@ -513,7 +513,8 @@ int finish(sieve_ctx *ctx, LaunchBuffers &lb, size_t m, int *overflowed) {
     CK(cudaMemcpyAsync(lb.h_acc, lb.d_acc + 1, (m + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if (lb.h_acc[m] & 2ull) return fail(ctx, SIEVE_EDEVICE, "a device-side wait hit its limit");
+    if ((lb.h_acc[m] & 2ull) || ctx->params.fault_wait)
+        return fail(ctx, SIEVE_EDEVICE, "a device-side wait hit its limit");
     *overflowed = (lb.h_acc[m] & 1ull) != 0;
     return SIEVE_OK;
 }
@@ -1025,6 +1026,10 @@ int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
             if (v < 0 || v > 2) return fail(ctx, SIEVE_EINVAL, "batch order (0, 1 or 2)");
             p.batch_order = (int)v;
             break;
+        case SIEVE_PARAM_FAULT_WAIT:
+            if (v != 0 && v != 1) return fail(ctx, SIEVE_EINVAL, "fault hook (0 or 1)");
+            p.fault_wait = (int)v;
+            break;
         case SIEVE_PARAM_SMALL_LIMIT_210:
             if (v < 0 || v > (1 << 20)) return fail(ctx, SIEVE_EINVAL, "small limit (mod 210)");
             p.small_limit210 = (uint32_t)v;
@@ -1055,6 +1060,7 @@ int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
         case SIEVE_PARAM_MID_LIMIT: *v = p.mid_limit; return SIEVE_OK;
         case SIEVE_PARAM_WHEEL: *v = p.wheel; return SIEVE_OK;
         case SIEVE_PARAM_BATCH_ORDER: *v = p.batch_order; return SIEVE_OK;
+        case SIEVE_PARAM_FAULT_WAIT: *v = p.fault_wait; return SIEVE_OK;
         case SIEVE_PARAM_SMALL_LIMIT_210: *v = p.small_limit210; return SIEVE_OK;
         case SIEVE_PARAM_MID_LIMIT_210: *v = p.mid_limit210; return SIEVE_OK;
         default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");
@@ -1076,6 +1082,23 @@ int sieve_base_primes(sieve_ctx *ctx, uint32_t *out, size_t cap, uint64_t *n) {
     if (!ctx || !n) return SIEVE_EINVAL;
     *n = ctx->h_primes.size();
     if (out) std::memcpy(out, ctx->h_primes.data(), std::min<size_t>(cap, ctx->h_primes.size()) * sizeof(uint32_t));
+    return SIEVE_OK;
+}
+
+int sieve_selftest_wait(sieve_ctx *ctx, int arm, uint32_t limit, int *timed_out) {
+    if (!ctx || !timed_out || limit == 0) return SIEVE_EINVAL;
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    int *d_status = nullptr;
+    rc = dev_alloc(ctx, &d_status, 1);
+    if (rc) return rc;
+    int h_status = -1;
+    cudaError_t e = launch_wait_selftest(ctx->d_tile, 4096, arm ? 1 : 0, limit, d_status, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, d_status, 1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "wait self-test");
+    *timed_out = h_status;
     return SIEVE_OK;
 }
 

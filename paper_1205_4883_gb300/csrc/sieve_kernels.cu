@@ -343,6 +343,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // thread for a while): far beyond any copy of a few hundred KB from L2.
 constexpr uint32_t kWaitLimit = 1u << 24;
 
+// Self-test of the bounded wait: one CTA initialises an mbarrier, copies `bytes`
+// from `src` into shared memory with the bulk copy when `arm` is set (else
+// nothing will ever complete the phase), and every thread waits with the given
+// limit.  *status = 0 when the phase completed, 1 when the limit was hit.
+__global__ void k_wait_selftest(const uint4 *src, uint32_t bytes, int arm, uint32_t limit, int *status) {
+    extern __shared__ uint4 buf[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t failed;
+    if (threadIdx.x == 0) {
+        failed = 0;
+        mbar_init(&bar, 1);
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && arm) bulk_copy_g2s(buf, src, bytes, &bar);
+    uint32_t tries = 0;
+    while (!mbar_try_wait(&bar, 0) && ++tries < limit) {
+    }
+    if (tries >= limit) failed = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) *status = failed ? 1 : 0;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict__ Pg) {
     extern __shared__ uint4 smem4[];
@@ -873,4 +896,12 @@ cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
+}  // namespace gbs
+
+namespace gbs {
+cudaError_t launch_wait_selftest(const void *src, uint32_t bytes, int arm, uint32_t limit, int *status_dev,
+                                 cudaStream_t stream) {
+    k_wait_selftest<<<1, 256, bytes, stream>>>(static_cast<const uint4 *>(src), bytes, arm, limit, status_dev);
+    return cudaGetLastError();
+}
 }  // namespace gbs

@@ -161,6 +161,24 @@ def test_tier_limits_do_not_change_results(mid):
             assert np.array_equal(words.cpu().numpy().view(np.uint32), oracle.bitmap(lo, hi)), (lo, hi)
 
 
+def test_bounded_device_wait_and_fault_hook(sv):
+    # the bounded mbarrier wait of the bulk shared-memory copies: it completes when a copy
+    # arrives, and when nothing ever completes the barrier it runs out after the limit and
+    # returns (no trap, no hang); the context stays usable afterwards
+    assert gb.sieve_selftest_wait(sv.ctx, True, 1 << 20) is False
+    assert gb.sieve_selftest_wait(sv.ctx, False, 2000) is True
+    assert sv.count(0, 10**6) == 78498
+    # the host's handling of a device-side wait failure, injected on the host
+    sv.set_param(gb.SIEVE_PARAM_FAULT_WAIT, 1)
+    try:
+        with pytest.raises(gb.SieveError) as e:
+            sv.count(0, 10**6)
+        assert e.value.code == gb.SIEVE_EDEVICE
+    finally:
+        sv.set_param(gb.SIEVE_PARAM_FAULT_WAIT, 0)
+    assert sv.count(0, 10**6) == 78498
+
+
 def test_large_lo_against_miller_rabin(sv):
     lo, hi = 10**14, 10**14 + 60_000
     got = [int(v) for v in sv.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)]
