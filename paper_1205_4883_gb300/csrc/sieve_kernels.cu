@@ -673,12 +673,20 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                 // 4. popcount of the bits in [lo, hi); a range on the Miller-Rabin
                 //    path also leaves its raw wheel words for k_mr_filter
                 uint32_t *const raw = rd.mr ? rd.bitmap : nullptr;
-                for (uint32_t w = tid; w < L / 4; w += blockDim.x) {
-                    uint32_t v = seg32[w];
-                    if (raw) raw[w] = v;
-                    const int64_t wb = 120 * (int64_t)w;
-                    if (wb < lo_rel || wb + 120 > hi_rel) v &= range_mask(wb, lo_rel, hi_rel);
-                    cnt += __popc(v);
+                if (!raw && lo_rel <= 0 && hi_rel >= 30 * (int64_t)L) {
+                    // the whole segment lies in [lo, hi): no masks, 16-byte loads
+                    for (uint32_t q = tid; q < L / 16; q += blockDim.x) {
+                        const uint4 v = smem4[q];
+                        cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+                    }
+                } else {
+                    for (uint32_t w = tid; w < L / 4; w += blockDim.x) {
+                        uint32_t v = seg32[w];
+                        if (raw) raw[w] = v;
+                        const int64_t wb = 120 * (int64_t)w;
+                        if (wb < lo_rel || wb + 120 > hi_rel) v &= range_mask(wb, lo_rel, hi_rel);
+                        cnt += __popc(v);
+                    }
                 }
             } else {
                 // 4'. each group of 32 wheel bytes (960 integers) is 15 words of the
