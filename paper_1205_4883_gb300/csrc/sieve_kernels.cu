@@ -665,8 +665,10 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             __syncthreads();
 
             // 3. the byte holding integers 0..29: 1 is not prime, 7..19 are
-            if (tid == 0 && B0 <= 0 && B0 + (int64_t)L > 0) seg[-B0] = 0xFE;
-            __syncthreads();
+            if (B0 <= 0 && B0 + (int64_t)L > 0) {  // the same for the whole CTA
+                if (tid == 0) seg[-B0] = 0xFE;
+                __syncthreads();
+            }
 
             unsigned long long cnt = 0;
             if (MODE == kModeCount) {
