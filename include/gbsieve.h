@@ -265,6 +265,10 @@ void sieve_server_destroy(sieve_server *srv);
 #define SIEVE_PARAM_FAULT_WAIT    14 /* test hook: 1 = synchronous calls report the failure of a
                                         device-side wait (SIEVE_EDEVICE) after their launch, as the
                                         sieve does when a bounded wait in a kernel runs out */
+#define SIEVE_PARAM_PRESIEVE      15 /* mod-30 kernels: largest prime whose multiples come from
+                                        pre-sieved patterns ANDed into each segment instead of being
+                                        crossed: 19 (one pattern, 7..19) or 59 (default: three further
+                                        patterns, 23..31, 37..43 and 47..59); results are the same */
 #define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
                                        primes, carried across the segments of a work item; used
                                        when they fit and enough segments resume one (half of a

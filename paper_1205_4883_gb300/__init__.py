@@ -40,6 +40,7 @@ SIEVE_PARAM_SMALL_LIMIT_210 = 11
 SIEVE_PARAM_MID_LIMIT_210 = 12
 SIEVE_PARAM_BATCH_ORDER = 13
 SIEVE_PARAM_FAULT_WAIT = 14
+SIEVE_PARAM_PRESIEVE = 15
 
 _u64 = ctypes.c_uint64
 _i64 = ctypes.c_int64
@@ -458,7 +459,7 @@ class Sieve:
                   "cursor_mb": SIEVE_PARAM_CURSOR_MB, "mr_percent": SIEVE_PARAM_MR_PERCENT,
                   "mid_limit": SIEVE_PARAM_MID_LIMIT, "wheel": SIEVE_PARAM_WHEEL,
                   "small_limit_210": SIEVE_PARAM_SMALL_LIMIT_210, "mid_limit_210": SIEVE_PARAM_MID_LIMIT_210,
-                  "batch_order": SIEVE_PARAM_BATCH_ORDER}
+                  "batch_order": SIEVE_PARAM_BATCH_ORDER, "presieve": SIEVE_PARAM_PRESIEVE}
 
     def apply_plan(self, plan: dict) -> None:
         """Set the launch parameters of an autotuned plan (see autotune.py)."""

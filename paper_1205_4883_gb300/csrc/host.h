@@ -29,6 +29,7 @@ struct Params {
     uint32_t mid_limit210 = 0;           // mod-210: primes below this use per-class sub-progressions; 0: words / 6
     int batch_order = 0;                 // batches: 0 as given, 1 heaviest first, 2 heaviest/lightest alternating
     int fault_wait = 0;                  // test hook: synchronous launches report a device-wait failure
+    uint32_t presieve = 59;              // mod-30: largest prime applied as a pattern (19 or 59)
 };
 
 // Everything one sieve launch reads and writes besides the resident state:

@@ -21,12 +21,28 @@ constexpr uint32_t kMaxSegmentBytes = 229376u;
 // Most segments one work item (a chunk) may hold; bucket lists are per segment of a chunk.
 constexpr uint32_t kMaxChunkSegments = 64u;
 // Small primes whose per-segment residue B0 mod p is cached in shared memory.
-constexpr uint32_t kSmallResidues = 288u;
+constexpr uint32_t kSmallResidues = 160u;
 // Number of byte-shifted copies of the pattern (one per 16-byte phase).
 constexpr uint32_t kTileCopies = 16u;
 // Index of the first base prime >= 23 in the base-prime array (2, 3, 5, 7,
 // 11, 13, 17, 19 come first).
 constexpr uint32_t kFirstCrossingPrime = 8u;
+// Three further pre-sieve patterns for the mod-30 kernels, ANDed into a segment
+// after the first one: the wheel bytes of 23 * 29 * 31, 37 * 41 * 43 and 47 * 53 * 59.
+// Each is stored like the first (kTileCopies byte-shifted copies, each a period
+// plus a full segment long), after it in the same allocation.
+constexpr uint32_t kXTilePeriod0 = 20677u;  // 23 * 29 * 31
+constexpr uint32_t kXTilePeriod1 = 65231u;  // 37 * 41 * 43
+constexpr uint32_t kXTilePeriod2 = 146969u; // 47 * 53 * 59
+constexpr uint64_t tile_copy_bytes(uint32_t period) {
+    return ((uint64_t)period + kMaxSegmentBytes + 32 + 15) & ~15ull;
+}
+constexpr uint64_t kXTileStride0 = tile_copy_bytes(kXTilePeriod0);
+constexpr uint64_t kXTileStride1 = tile_copy_bytes(kXTilePeriod1);
+constexpr uint64_t kXTileStride2 = tile_copy_bytes(kXTilePeriod2);
+// Index of the first base prime >= 61: the first one crossed when the
+// further patterns are applied.
+constexpr uint32_t kFirstCrossingPrimeX = 17u;
 
 // One range of a launch.  Segment s of the range covers wheel bytes
 // [Bbase + s S, Bbase + (s + 1) S); Bbase is chosen so that 30 Bbase + 1 is
@@ -56,7 +72,7 @@ struct SieveLaunch {
     unsigned long long *counts;          // one per range, zeroed before the launch
     const uint32_t *primes;              // base primes, ascending, 2 first
     const uint64_t *magic;               // floor((2^64 - 1) / p) per prime
-    uint32_t small_end;                  // primes [8, small_end) crossed warp-cooperatively
+    uint32_t small_end;                  // primes [small_first, small_end) crossed warp-cooperatively
     uint32_t mid_end;                    // primes [small_end, mid_end): per-phase sub-progressions
     uint32_t bucket_first;               // primes [bucket_first, ...) go through the bucket lists
     uint32_t chunk_segs;                 // segments per work item, <= kMaxChunkSegments
@@ -72,6 +88,9 @@ struct SieveLaunch {
     const uint8_t *tile;                 // kTileCopies shifted copies of the pattern
     uint64_t tile_stride;                // bytes between copies
     uint32_t seg_bytes;                  // S, multiple of 32, <= kMaxSegmentBytes
+    uint32_t small_first;                // first prime of the small tier: kFirstCrossingPrime, or
+                                         // kFirstCrossingPrimeX with the further patterns
+    const uint8_t *xtile0, *xtile1, *xtile2;  // null, or copy 0 of each further pattern (mod-30 kernels)
 };
 // Bytes reserved for the SieveLaunch at the head of a launch block; the
 // RangeDescs follow it.
@@ -80,7 +99,10 @@ static_assert(sizeof(SieveLaunch) <= kLaunchHeader, "launch header");
 
 // Kernel launchers (sieve_kernels.cu).  All enqueue on `stream` and return the
 // CUDA launch status.
-cudaError_t launch_build_tile(uint8_t *tile, uint64_t stride, uint32_t len, cudaStream_t stream);
+// Pattern of the primes ps[0 .. np) (np <= 5, product = period) on the mod-30 wheel:
+// kTileCopies copies, copy k holding pattern byte (i + k) mod period at offset i < len.
+cudaError_t launch_build_tile(uint8_t *tile, uint64_t stride, uint32_t len, uint32_t period, const uint32_t *ps,
+                              int np, cudaStream_t stream);
 cudaError_t launch_tiny_primes(uint32_t *out, uint32_t *n_out, cudaStream_t stream);
 cudaError_t launch_magic(const uint32_t *primes, uint64_t *magic, uint64_t n, cudaStream_t stream);
 // Launch parameters live in device memory (d_launch) so that a captured graph

@@ -303,6 +303,14 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
     L.magic = ctx->d_magic;
     L.tile = ctx->d_tile;
     L.tile_stride = ctx->tile_stride;
+    if (prm.presieve == 59) {
+        L.xtile0 = ctx->d_tile + ctx->tile_stride * kTileCopies;
+        L.xtile1 = L.xtile0 + kXTileStride0 * kTileCopies;
+        L.xtile2 = L.xtile1 + kXTileStride1 * kTileCopies;
+        L.small_first = kFirstCrossingPrimeX;
+    } else {
+        L.small_first = kFirstCrossingPrime;
+    }
     L.seg_bytes = prm.seg_bytes;
     L.chunk_segs = C;
     L.small_end = small_end;
@@ -436,6 +444,7 @@ int prepare_launch210(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size
     L.primes = ctx->d_primes;
     L.magic = ctx->d_magic;
     L.seg_bytes = 4 * sw;
+    L.small_first = kFirstCrossingPrime;
     L.chunk_segs = C;
     L.small_end = small_end;
     L.mid_end = mid_end;
@@ -767,13 +776,26 @@ int sieve_create(sieve_ctx **out, uint64_t hi_max, int device, void *cuda_stream
     }
     e = set_sieve_smem_limits();
     if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "cudaFuncSetAttribute"));
-    // pattern tile: 16 copies, each long enough for any phase plus a full segment
-    const uint64_t len = ((uint64_t)kTilePeriod + kMaxSegmentBytes + 32 + 15) & ~15ull;
+    // pattern tiles: 16 copies each, each long enough for any phase plus a full
+    // segment; the primes 7..19, then the further patterns 23..31, 37..43, 47..59
+    const uint64_t len = tile_copy_bytes(kTilePeriod);
     ctx->tile_stride = len;
-    int rc = dev_alloc(ctx, &ctx->d_tile, len * kTileCopies);
+    int rc = dev_alloc(ctx, &ctx->d_tile, (len + kXTileStride0 + kXTileStride1 + kXTileStride2) * kTileCopies);
     if (rc) return bail(rc);
-    e = launch_build_tile(ctx->d_tile, ctx->tile_stride, (uint32_t)len, ctx->stream);
-    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "build tile"));
+    {
+        static const uint32_t pa[] = {7, 11, 13, 17, 19}, pb[] = {23, 29, 31}, pc[] = {37, 41, 43},
+                              pd[] = {47, 53, 59};
+        uint8_t *x0 = ctx->d_tile + len * kTileCopies, *x1 = x0 + kXTileStride0 * kTileCopies,
+                *x2 = x1 + kXTileStride1 * kTileCopies;
+        e = launch_build_tile(ctx->d_tile, len, (uint32_t)len, kTilePeriod, pa, 5, ctx->stream);
+        if (e == cudaSuccess) e = launch_build_tile(x0, kXTileStride0, (uint32_t)kXTileStride0, kXTilePeriod0, pb, 3,
+                                                    ctx->stream);
+        if (e == cudaSuccess) e = launch_build_tile(x1, kXTileStride1, (uint32_t)kXTileStride1, kXTilePeriod1, pc, 3,
+                                                    ctx->stream);
+        if (e == cudaSuccess) e = launch_build_tile(x2, kXTileStride2, (uint32_t)kXTileStride2, kXTilePeriod2, pd, 3,
+                                                    ctx->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "build tile"));
+    }
     // the mod-210 count path: class tables and the 16 shifted copies of its pattern
     {
         e = set_sieve210_smem_limit();
@@ -1030,6 +1052,10 @@ int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
             if (v != 0 && v != 1) return fail(ctx, SIEVE_EINVAL, "fault hook (0 or 1)");
             p.fault_wait = (int)v;
             break;
+        case SIEVE_PARAM_PRESIEVE:
+            if (v != 19 && v != 59) return fail(ctx, SIEVE_EINVAL, "pre-sieve limit (19 or 59)");
+            p.presieve = (uint32_t)v;
+            break;
         case SIEVE_PARAM_SMALL_LIMIT_210:
             if (v < 0 || v > (1 << 20)) return fail(ctx, SIEVE_EINVAL, "small limit (mod 210)");
             p.small_limit210 = (uint32_t)v;
@@ -1061,6 +1087,7 @@ int sieve_get_param(sieve_ctx *ctx, int param, int64_t *v) {
         case SIEVE_PARAM_WHEEL: *v = p.wheel; return SIEVE_OK;
         case SIEVE_PARAM_BATCH_ORDER: *v = p.batch_order; return SIEVE_OK;
         case SIEVE_PARAM_FAULT_WAIT: *v = p.fault_wait; return SIEVE_OK;
+        case SIEVE_PARAM_PRESIEVE: *v = p.presieve; return SIEVE_OK;
         case SIEVE_PARAM_SMALL_LIMIT_210: *v = p.small_limit210; return SIEVE_OK;
         case SIEVE_PARAM_MID_LIMIT_210: *v = p.mid_limit210; return SIEVE_OK;
         default: return fail(ctx, SIEVE_EINVAL, "unknown parameter");

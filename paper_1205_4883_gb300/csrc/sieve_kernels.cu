@@ -366,6 +366,48 @@ __global__ void k_wait_selftest(const uint4 *src, uint32_t bytes, int arm, uint3
     if (threadIdx.x == 0) *status = failed ? 1 : 0;
 }
 
+// Medium primes [base, base + 32) below mid_end, lane l taking base + l, over
+// the L bytes (a multiple of 32) at wheel byte B0 held at seg32: each of a
+// prime's eight progressions (stride p bytes) is split into four
+// sub-progressions of stride 4 p bytes = p words, one per byte phase, each
+// crossed with one fixed mask.  The warp re-converges after every sub-loop.
+__device__ __forceinline__ void cross_medium_group(const WheelTables &tab, const uint32_t *__restrict__ primes,
+                                                   const uint64_t *__restrict__ magic, uint32_t *seg32,
+                                                   uint32_t base, uint32_t mid_end, int lane, int64_t B0,
+                                                   uint32_t L) {
+    const uint64_t Bc = B0 > 0 ? (uint64_t)B0 : 0;
+    const uint32_t i = base + lane;
+    const bool valid = i < mid_end;
+    const uint32_t p = valid ? __ldg(primes + i) : 1u;
+    const uint64_t M = valid ? __ldg(magic + i) : ~0ull;
+    const uint32_t R = mod_barrett(Bc, p, M);
+    const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
+    const bool early = valid && is_early(B0, Bc, p);
+    if (early) cross_prime_early(tab, seg32, p, pq, pc, R, B0, L);
+    __syncwarp();
+    const uint32_t lw = (valid && !early) ? L >> 2 : 0u;  // fast path only for the others
+    const uint32_t bits = tab.bits24[pc];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, false, L);
+        const uint32_t bit = (bits >> (3 * j)) & 7u;
+#pragma unroll
+        for (uint32_t ph = 0; ph < 4; ++ph) {
+            // p^-1 = p (mod 4), so off + k p = ph (mod 4) for k = (ph - off) p mod 4
+            const uint32_t o = off + (((ph - off) * p) & 3u) * p;
+            const uint32_t mask = ~(1u << (8u * ph + bit));
+            for (uint32_t w = o >> 2; w < lw; w += p) atomicAnd(&seg32[w], mask);
+        }
+        __syncwarp();
+    }
+}
+
+// Medium groups whose estimated costs are kept in shared memory for dealing
+// them over the warps; the cost of a group is kMidSetup plus the hits of its
+// smallest prime in a full segment, 8 S / p.
+constexpr uint32_t kMidGroups = 128;
+constexpr uint32_t kMidSetup = 224;
+
 template <int MODE>
 __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict__ Pg) {
     extern __shared__ uint4 smem4[];
@@ -384,6 +426,9 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
     __shared__ uint32_t s_cnt[kMaxChunkSegments];  // bucket fill counts, one per segment of the chunk
     __shared__ __align__(8) uint64_t s_tile_bar;    // completes the pattern copy of each segment
     __shared__ uint32_t s_tile_fail;                // a wait for it hit kWaitLimit: the CTA stops
+    __shared__ uint32_t s_xph[3];                   // B0 mod the periods of the further patterns
+    __shared__ uint32_t s_midG;                     // medium groups dealt by cost (0: round-robin)
+    __shared__ uint32_t s_midW[kMidGroups + 1];     // their cumulative costs
     uint32_t tile_phase = 0;
     if (threadIdx.x == 0) {
         s_tile_fail = 0;
@@ -394,6 +439,22 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
     init_tables(tab);
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t S = P.seg_bytes, C = P.chunk_segs;
+    if (tid < 32) {  // cumulative costs of the medium groups (read after the next barrier)
+        const uint32_t ng = P.mid_end > P.small_end ? (P.mid_end - P.small_end + 31) / 32 : 0;
+        const uint32_t G = ng <= kMidGroups ? ng : 0;
+        uint32_t run = 0;
+        for (uint32_t g0 = 0; g0 < G; g0 += 32) {
+            const uint32_t g = g0 + lane;
+            const uint32_t c = g < G ? kMidSetup + 8u * S / __ldg(P.primes + P.small_end + 32u * g) : 0u;
+            const uint32_t incl = warp_inclusive_scan(c, lane);
+            if (g < G) s_midW[g + 1] = run + incl;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) {
+            s_midW[0] = 0;
+            s_midG = G;
+        }
+    }
     uint32_t *const bucket_base = P.buckets ? P.buckets + (size_t)blockIdx.x * C * P.bucket_cap : nullptr;
 
     for (;;) {
@@ -502,6 +563,13 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                 if (tid == 0) {
                     fence_proxy_async_smem();
                     bulk_copy_g2s(smem4, src, L, &s_tile_bar);
+                    if (P.xtile0) {
+                        const int64_t x0 = B0 % (int64_t)kXTilePeriod0, x1 = B0 % (int64_t)kXTilePeriod1,
+                                      x2 = B0 % (int64_t)kXTilePeriod2;
+                        s_xph[0] = (uint32_t)(x0 < 0 ? x0 + kXTilePeriod0 : x0);
+                        s_xph[1] = (uint32_t)(x1 < 0 ? x1 + kXTilePeriod1 : x1);
+                        s_xph[2] = (uint32_t)(x2 < 0 ? x2 + kXTilePeriod2 : x2);
+                    }
                 }
             }
             // primes with p^2 >= the segment's end have no multiple to cross here
@@ -514,12 +582,12 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                     s_small_next = 0;
                 }
             }
+            const uint32_t small_first = P.small_first;
             {
                 const uint32_t se = P.small_end < n_range ? P.small_end : n_range;
-                const uint32_t nr = se > kFirstCrossingPrime ? se - kFirstCrossingPrime : 0;
+                const uint32_t nr = se > small_first ? se - small_first : 0;
                 for (uint32_t t = tid; t < nr && t < kSmallResidues; t += blockDim.x)
-                    s_R[t] = mod_barrett(Bc, __ldg(P.primes + kFirstCrossingPrime + t),
-                                         __ldg(P.magic + kFirstCrossingPrime + t));
+                    s_R[t] = mod_barrett(Bc, __ldg(P.primes + small_first + t), __ldg(P.magic + small_first + t));
             }
             {
                 uint32_t tries = 0;
@@ -530,45 +598,69 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             }
             __syncthreads();
             if (s_tile_fail) break;  // every thread sees it after the barrier
+            // 1'. the further patterns (primes 23..59), ANDed in 16 bytes at a time
+            //     from their L2-resident shifted copies
+            if (P.xtile0) {
+                const uint4 *x0 = reinterpret_cast<const uint4 *>(P.xtile0 + (s_xph[0] & 15u) * kXTileStride0 +
+                                                                  (s_xph[0] & ~15u));
+                const uint4 *x1 = reinterpret_cast<const uint4 *>(P.xtile1 + (s_xph[1] & 15u) * kXTileStride1 +
+                                                                  (s_xph[1] & ~15u));
+                const uint4 *x2 = reinterpret_cast<const uint4 *>(P.xtile2 + (s_xph[2] & 15u) * kXTileStride2 +
+                                                                  (s_xph[2] & ~15u));
+                for (uint32_t q = tid; q < L / 16; q += blockDim.x) {
+                    const uint4 a = __ldg(x0 + q), b = __ldg(x1 + q), c = __ldg(x2 + q);
+                    uint4 v = smem4[q];
+                    v.x &= a.x & b.x & c.x;
+                    v.y &= a.y & b.y & c.y;
+                    v.z &= a.z & b.z & c.z;
+                    v.w &= a.w & b.w & c.w;
+                    smem4[q] = v;
+                }
+                __syncthreads();
+            }
             // a range on the Miller-Rabin path is sieved with the primes below 2^16 only
             const uint32_t n_seg = rd.mr && P.mr_end < s_nseg ? P.mr_end : s_nseg;
             // primes crossed here (not through the buckets): [8, n_use)
             const uint32_t n_use = use_buckets && P.bucket_first < n_seg ? P.bucket_first : n_seg;
             const uint32_t small_end = P.small_end < n_use ? P.small_end : n_use;
-            const uint32_t n_small8 = (small_end > kFirstCrossingPrime ? small_end - kFirstCrossingPrime : 0) * 8;
+            const uint32_t n_small8 = (small_end > small_first ? small_end - small_first : 0) * 8;
 
-            // 2a. medium primes [small_end, mid_end): one lane per prime, the warp
-            //     taking 32 consecutive primes at a time (warp-uniform loop, so
-            //     the lanes can be re-converged after every sub-loop).  Each of
-            //     the eight progressions (stride p bytes) is split into four
-            //     sub-progressions of stride 4 p bytes = p words, one per byte
-            //     phase, each crossed with one fixed mask.
+            // 2a. medium primes [small_end, mid_end), 32 consecutive primes (a group)
+            //     at a time.  The groups are dealt by estimated cost: warp w takes the
+            //     w-th 1/32 of the cumulative cost, so a heavy group (small primes,
+            //     many hits) is shared by several warps, each crossing it over its
+            //     own part of the segment.
             const uint32_t mid_end = P.mid_end < n_use ? P.mid_end : n_use;
             const uint32_t Lw = L >> 2;
-            for (uint32_t base = P.small_end + (tid & ~31u); base < mid_end; base += blockDim.x) {
-                const uint32_t i = base + lane;
-                const bool valid = i < mid_end;
-                const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
-                const uint64_t M = valid ? __ldg(P.magic + i) : ~0ull;
-                const uint32_t R = mod_barrett(Bc, p, M);
-                const uint32_t pq = p / 30, pc = valid ? tab.cls[p - pq * 30] : 0u;
-                const bool early = valid && is_early(B0, Bc, p);
-                if (early) cross_prime_early(tab, seg32, p, pq, pc, R, B0, L);
-                __syncwarp();
-                const uint32_t lw = (valid && !early) ? Lw : 0u;  // fast path only for the others
-                const uint32_t bits = tab.bits24[pc];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, false, L);
-                    const uint32_t bit = (bits >> (3 * j)) & 7u;
-#pragma unroll
-                    for (uint32_t ph = 0; ph < 4; ++ph) {
-                        // p^-1 = p (mod 4), so off + k p = ph (mod 4) for k = (ph - off) p mod 4
-                        const uint32_t o = off + (((ph - off) * p) & 3u) * p;
-                        const uint32_t mask = ~(1u << (8u * ph + bit));
-                        for (uint32_t w = o >> 2; w < lw; w += p) atomicAnd(&seg32[w], mask);
+            {
+                // G > 0: warp w takes the cost interval [x0, x1); G = 0 (too many
+                // groups for the table): warp w takes groups w, w + 32, ... whole
+                const uint32_t G = s_midG, warp = tid >> 5, nwarps = blockDim.x >> 5;
+                const uint32_t T = s_midW[G];
+                const uint32_t x0 = (uint32_t)((uint64_t)T * warp / nwarps);
+                const uint32_t x1 = (uint32_t)((uint64_t)T * (warp + 1) / nwarps);
+                uint32_t g = warp;
+                if (G) {
+                    uint32_t hi = G - 1;  // the last group with W[g] <= x0
+                    g = 0;
+                    while (g < hi) {
+                        const uint32_t mid = (g + hi + 1) >> 1;
+                        if (s_midW[mid] <= x0) g = mid; else hi = mid - 1;
                     }
-                    __syncwarp();
+                }
+                for (;; g += G ? 1u : nwarps) {
+                    const uint32_t base = P.small_end + 32u * g;
+                    if (base >= mid_end || (G && (g >= G || s_midW[g] >= x1))) break;
+                    uint32_t a = 0, b = L;
+                    if (G) {
+                        // part [a, b) of the segment, cut at 32-byte boundaries that
+                        // the neighbouring warp computes the same way
+                        const uint32_t w0 = s_midW[g], wg = s_midW[g + 1] - w0;
+                        const uint32_t u0 = (x0 > w0 ? x0 : w0) - w0, u1 = (x1 < w0 + wg ? x1 : w0 + wg) - w0;
+                        a = (uint32_t)(((uint64_t)u0 * L / wg) & ~31ull);
+                        b = (uint32_t)(((uint64_t)u1 * L / wg) & ~31ull);
+                    }
+                    if (a < b) cross_medium_group(tab, P.primes, P.magic, seg32 + a / 4, base, mid_end, lane, B0 + a, b - a);
                 }
             }
             // 2a'. large primes below the bucket limit [mid_end, n_use): one lane
@@ -624,7 +716,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                     atomicAnd(&seg32[v & 0xffffu], ~(1u << (v >> 16)));
                 }
             }
-            // 2b. small primes [8, small_end): one (prime, class) progression per
+            // 2b. small primes [small_first, small_end): one (prime, class) progression per
             //     warp, taken dynamically in decreasing order of work.  The
             //     progression (stride p bytes) is split into 128 sub-progressions
             //     of stride 128 p: lane l takes the four whose bytes are 4 l + q
@@ -636,10 +728,10 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                 if (lane == 0) k = atomicAdd(&s_small_next, 1u);
                 k = __shfl_sync(0xffffffffu, k, 0);
                 if (k >= n_small8) break;
-                const uint32_t i = kFirstCrossingPrime + (k >> 3);
+                const uint32_t i = small_first + (k >> 3);
                 const int j = (int)(k & 7);
                 const uint32_t p = __ldg(P.primes + i);
-                const uint32_t t = i - kFirstCrossingPrime;
+                const uint32_t t = i - small_first;
                 const uint32_t R = t < kSmallResidues ? s_R[t] : mod_barrett(Bc, p, __ldg(P.magic + i));
                 const uint32_t pq = p / 30, pc = tab.cls[p - pq * 30];
                 const uint32_t off = class_off(tab, p, pq, pc, j, R, B0, is_early(B0, Bc, p), L);
@@ -664,9 +756,13 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             }
             __syncthreads();
 
-            // 3. the byte holding integers 0..29: 1 is not prime, 7..19 are
-            if (B0 <= 0 && B0 + (int64_t)L > 0) {  // the same for the whole CTA
-                if (tid == 0) seg[-B0] = 0xFE;
+            // 3. wheel bytes 0 and 1 (integers 1..59): 1 and 49 are not prime, the
+            //    others are, though the patterns clear 7..19 and 23..59
+            if (B0 <= 1 && B0 + (int64_t)L > 0) {  // the same for the whole CTA
+                if (tid == 0) {
+                    if (B0 <= 0) seg[-B0] = 0xFE;
+                    if (1 - B0 < (int64_t)L) seg[1 - B0] = 0xDF;
+                }
                 __syncthreads();
             }
 
@@ -800,17 +896,24 @@ __global__ void __launch_bounds__(256) k_mr_filter(const SieveLaunch *__restrict
 
 // ---------------------------------------------------------------- pattern tile
 
-// Copy k (k = blockIdx.y) holds pattern bytes (i + k) mod 323323 at offset i.
-// Pattern byte b, bit j: 1 iff 30 b + r_j has no prime factor among 7..19.
-__global__ void k_build_tile(uint8_t *tile, uint64_t stride, uint32_t len) {
+// Copy k (k = blockIdx.y) holds pattern bytes (i + k) mod period at offset i.
+// Pattern byte b, bit j: 1 iff 30 b + r_j has no prime factor among the np
+// primes of ps, whose product is the period.
+struct TilePrimes {
+    uint32_t p[5];
+};
+
+__global__ void k_build_tile(uint8_t *tile, uint64_t stride, uint32_t len, uint32_t period, TilePrimes ps, int np) {
     const uint32_t k = blockIdx.y;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
-        const uint32_t b = (i + k) % kTilePeriod;
+        const uint32_t b = (uint32_t)(((uint64_t)i + k) % period);
         uint32_t v = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const uint32_t n = 30u * b + c_res[j];
-            if (n % 7u && n % 11u && n % 13u && n % 17u && n % 19u) v |= 1u << j;
+            const uint64_t n = 30ull * b + c_res[j];
+            bool keep = true;
+            for (int t = 0; t < np; ++t) keep = keep && n % ps.p[t] != 0;
+            if (keep) v |= 1u << j;
         }
         tile[k * stride + i] = (uint8_t)v;
     }
@@ -873,9 +976,13 @@ cudaError_t launch_mr_filter(int mode, const SieveLaunch *d_launch, int grid, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_tile(uint8_t *tile, uint64_t stride, uint32_t len, cudaStream_t stream) {
+cudaError_t launch_build_tile(uint8_t *tile, uint64_t stride, uint32_t len, uint32_t period, const uint32_t *ps,
+                              int np, cudaStream_t stream) {
+    if (np < 1 || np > 5) return cudaErrorInvalidValue;
+    TilePrimes t{};
+    for (int i = 0; i < np; ++i) t.p[i] = ps[i];
     dim3 grid((len + 255) / 256 < 4096 ? (len + 255) / 256 : 4096, kTileCopies);
-    k_build_tile<<<grid, 256, 0, stream>>>(tile, stride, len);
+    k_build_tile<<<grid, 256, 0, stream>>>(tile, stride, len, period, t, np);
     return cudaGetLastError();
 }
 

@@ -161,6 +161,25 @@ def test_tier_limits_do_not_change_results(mid):
             assert np.array_equal(words.cpu().numpy().view(np.uint32), oracle.bitmap(lo, hi)), (lo, hi)
 
 
+@pytest.mark.parametrize("presieve", [19, 59])
+@pytest.mark.parametrize("small", [23, 61, 512])
+def test_presieve_patterns_do_not_change_results(presieve, small):
+    # primes 23..59 crossed one by one (19) or ANDed in as three patterns (59), with the
+    # small tier starting below, at or above the first prime it crosses; wheel bytes
+    # 0 and 1 (integers 1..59) hold primes the patterns clear
+    with gb.Sieve(10**13) as s:
+        s.set_param(gb.SIEVE_PARAM_PRESIEVE, presieve)
+        s.set_param(gb.SIEVE_PARAM_SMALL_LIMIT, small)
+        assert s.get_param(gb.SIEVE_PARAM_PRESIEVE) == presieve
+        for lo, hi in [(0, 10**7), (0, 60), (1, 61), (30, 90), (31, 32), (47, 48), (49, 50), (53, 60),
+                       (5, 40_000), (10**12 - 10**6, 10**12 + 10**6), (9 * 10**12, 9 * 10**12 + 2 * 10**7)]:
+            assert s.count(lo, hi) == oracle.count(lo, hi), (lo, hi)
+            words, _ = s.bitmap(lo, hi)
+            assert np.array_equal(words.cpu().numpy().view(np.uint32), oracle.bitmap(lo, hi)), (lo, hi)
+        with pytest.raises(gb.SieveError):
+            s.set_param(gb.SIEVE_PARAM_PRESIEVE, 47)
+
+
 def test_bounded_device_wait_and_fault_hook(sv):
     # the bounded mbarrier wait of the bulk shared-memory copies: it completes when a copy
     # arrives, and when nothing ever completes the barrier it runs out after the limit and
