@@ -34,7 +34,7 @@ METRIC = "integers sieved/s"
 # DRAM bytes (read + write) of one k_sieve<0> launch on this workload, from
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass, full launch);
 # reported only while the kernel source is the one it was measured on.
-TRAFFIC = {"kernel_sha256_16": "b26d7ba6a76f9d5c", "bytes": 28.77e6 + 447.25e6}
+TRAFFIC = {"kernel_sha256_16": "9f0b40c125b536dd", "bytes": 27.76e6 + 209.36e6}
 WORKLOAD = "pi(10^12): count primes in [0, 10^12), one range, count-only, mod-30 wheel + pattern of 7..19"
 
 

@@ -249,7 +249,7 @@ void sieve_server_destroy(sieve_server *srv);
                                        default 0 (off: measured slower) */
 #define SIEVE_PARAM_MID_LIMIT     9 /* primes from the small limit up to this are crossed one lane
                                        per prime with per-byte-phase sub-progressions, larger ones
-                                       by walking the wheel; 0 = segment bytes / 8 (default) */
+                                       by walking the wheel; 0 = segment bytes / 3 (default) */
 #define SIEVE_PARAM_WHEEL         10 /* count-only calls (sieve_count, sieve_count_dev,
                                         sieve_batch_count without bitmaps) sieve on the mod-30 wheel
                                         (30, default) or the mod-210 wheel (210: 48 bits per 210

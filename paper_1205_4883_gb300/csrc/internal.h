@@ -21,7 +21,7 @@ constexpr uint32_t kMaxSegmentBytes = 229376u;
 // Most segments one work item (a chunk) may hold; bucket lists are per segment of a chunk.
 constexpr uint32_t kMaxChunkSegments = 64u;
 // Small primes whose per-segment residue B0 mod p is cached in shared memory.
-constexpr uint32_t kSmallResidues = 160u;
+constexpr uint32_t kSmallResidues = 96u;
 // Number of byte-shifted copies of the pattern (one per 16-byte phase).
 constexpr uint32_t kTileCopies = 16u;
 // Index of the first base prime >= 23 in the base-prime array (2, 3, 5, 7,

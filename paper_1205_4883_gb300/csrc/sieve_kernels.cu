@@ -405,7 +405,7 @@ __device__ __forceinline__ void cross_medium_group(const WheelTables &tab, const
 // Medium groups whose estimated costs are kept in shared memory for dealing
 // them over the warps; the cost of a group is kMidSetup plus the hits of its
 // smallest prime in a full segment, 8 S / p.
-constexpr uint32_t kMidGroups = 128;
+constexpr uint32_t kMidGroups = 256;
 constexpr uint32_t kMidSetup = 224;
 
 template <int MODE>
