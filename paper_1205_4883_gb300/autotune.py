@@ -73,7 +73,7 @@ def sample_class(lo_band, w_band, n: int, seed: int, hi_max: int) -> Tuple[List[
 
 def candidates(quick: bool):
     segs = [65536, 229376] if quick else [32768, 65536, 131072, 229376]
-    smalls = [512] if quick else [256, 512, 896]
+    smalls = [448] if quick else [256, 448, 896]
     threads = [1024] if quick else [512, 1024]
     buckets = [1 << 62, 0]
     chunks = [16]

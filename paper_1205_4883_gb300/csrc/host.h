@@ -17,7 +17,7 @@ namespace gbs {
 struct Params {
     uint32_t seg_bytes = kMaxSegmentBytes;
     int threads = 1024;
-    uint32_t small_limit = 512;   // measured best on pi(10^12) among 64..1792
+    uint32_t small_limit = 448;   // measured best on pi(10^12) among 384..576 (64..1792 before the dealing by cost)
     uint32_t mid_limit = 0;       // primes below this use per-phase sub-progressions; 0: segment bytes / 3
     int ctas_per_sm = 1;
     uint32_t chunk_segs = 16;

@@ -326,3 +326,79 @@ def test_first_class_closed_form_mod30():
         R = rng.randrange(0, p)
         want = sum(1 for r in RES if p * r // 30 < R)
         assert (cnt[(30 * R - 1) // p] if R else 0) == want, (p, R)
+
+
+def deal_medium_parts(costs, nwarps, L):
+    """The medium tier's dealing by cost, as the kernel does it: warp w takes the
+    cost interval [T w / n, T (w + 1) / n) of the cumulative costs W, and of each
+    group g it overlaps the segment part [a, b), cut at 32-byte boundaries."""
+    W = [0]
+    for c in costs:
+        W.append(W[-1] + c)
+    G, T = len(costs), W[-1]
+    parts = []  # (warp, group, a, b)
+    for warp in range(nwarps):
+        x0, x1 = T * warp // nwarps, T * (warp + 1) // nwarps
+        g, hi = 0, G - 1  # the last group with W[g] <= x0 (binary search)
+        while g < hi:
+            mid = (g + hi + 1) >> 1
+            if W[mid] <= x0:
+                g = mid
+            else:
+                hi = mid - 1
+        while g < G and W[g] < x1:
+            w0, wg = W[g], W[g + 1] - W[g]
+            u0, u1 = max(x0, w0) - w0, min(x1, w0 + wg) - w0
+            a, b = (u0 * L // wg) & ~31, (u1 * L // wg) & ~31
+            if a < b:
+                parts.append((warp, g, a, b))
+            g += 1
+    return parts
+
+
+def test_medium_groups_dealt_by_cost_cover_each_segment_once():
+    # every group's parts, over all warps, tile [0, L) exactly, at 32-byte boundaries,
+    # and no warp's share of the estimated cost exceeds its 1/n by more than one part
+    rng = random.Random(1205)
+    primes = small_primes(90000)
+    for trial in range(300):
+        nwarps = rng.choice([8, 16, 32])
+        L = 32 * rng.randrange(1, 229376 // 32 + 1)
+        S = rng.choice([L, 229376])
+        first = rng.randrange(0, 200)
+        G = rng.randrange(1, 257)
+        costs = [224 + 8 * S // primes[min(first + 32 * g, len(primes) - 1)] for g in range(G)]
+        parts = deal_medium_parts(costs, nwarps, L)
+        by_group = {}
+        for warp, g, a, b in parts:
+            assert a % 32 == 0 and b % 32 == 0 and 0 <= a < b <= L
+            by_group.setdefault(g, []).append((a, b, warp))
+        assert sorted(by_group) == list(range(G)), trial
+        for g, ps in by_group.items():
+            ps.sort()
+            assert ps[0][0] == 0 and ps[-1][1] == L, (trial, g)
+            for (a0, b0, w0), (a1, b1, w1) in zip(ps, ps[1:]):
+                assert b0 == a1 and w0 < w1, (trial, g)
+    # the default tier (primes from 449, 232 groups): the first group costs more than a
+    # warp's share, so it is split, and every warp's estimated cost is within one
+    # part's setup of its share
+    costs = [224 + 8 * 229376 // primes[86 - 8 + 32 * g] for g in range(232)]
+    parts = deal_medium_parts(costs, 32, 229376)
+    share = sum(costs) / 32
+    assert costs[0] > share and len({w for w, g, a, b in parts if g == 0}) >= 2
+    for w in range(32):
+        est = sum(224 + (costs[g] - 224) * (b - a) / 229376 for ww, g, a, b in parts if ww == w)
+        n = sum(1 for ww, *_ in parts if ww == w)
+        assert est <= share + 224 * n + 32, (w, est, share)
+
+
+def test_fixup_of_wheel_bytes_0_and_1():
+    # after the patterns (7..19 and 23..59) every prime below 60 is cleared, so the
+    # kernel rewrites wheel bytes 0 (integers 1..29) and 1 (31..59) with their true value
+    def is_prime(n):
+        return n > 1 and all(n % d for d in range(2, int(n ** 0.5) + 1))
+    for byte, want in ((0, 0xFE), (1, 0xDF)):
+        v = sum(1 << k for k, r in enumerate(RES) if is_prime(30 * byte + r))
+        assert v == want, (byte, hex(v))
+    # no later wheel byte holds a pattern prime: byte 2 starts at 61
+    assert all(30 * 2 + r > 59 for r in RES)
