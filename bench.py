@@ -115,9 +115,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_sample(target_s: float = 12.0):
+def cpu_oracle_sample(target_s: float = 12.0, single_s: float = 3.0):
     """The oracle (unchanged) on the host cores, on a bounded sample of the
-    workload: the top of [0, 10^12), sized to about target_s seconds."""
+    workload: the top of [0, 10^12), sized to about target_s seconds; and on one
+    thread, sized to about single_s seconds."""
     import oracle
     oracle.build()
     cores = oracle.default_threads()
@@ -130,8 +131,21 @@ def cpu_oracle_sample(target_s: float = 12.0):
     t = time.perf_counter()
     c = oracle.count(UNITS - n, UNITS, cores)
     dt = time.perf_counter() - t
-    return {"value": n / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+    line = {"value": n / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
             "sample": f"count of [10^12 - {n}, 10^12) ({c} primes) on {cores} threads, {dt:.2f} s"}
+    # and on one thread, over a slice of about single_s seconds
+    probe = 2 * 10**7
+    t = time.perf_counter()
+    oracle.count(UNITS - probe, UNITS, 1)
+    dt = max(time.perf_counter() - t, 1e-3)
+    n1 = int(min(UNITS, max(probe, probe * single_s / dt)))
+    n1 -= n1 % 30
+    t = time.perf_counter()
+    c1 = oracle.count(UNITS - n1, UNITS, 1)
+    dt = time.perf_counter() - t
+    line["single_thread"] = {"value": n1 / dt, "unit": METRIC, "cores": 1,
+                             "sample": f"count of [10^12 - {n1}, 10^12) ({c1} primes) on 1 thread, {dt:.2f} s"}
+    return line
 
 
 def run_reference(args):
