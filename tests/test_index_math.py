@@ -402,3 +402,27 @@ def test_fixup_of_wheel_bytes_0_and_1():
         assert v == want, (byte, hex(v))
     # no later wheel byte holds a pattern prime: byte 2 starts at 61
     assert all(30 * 2 + r > 59 for r in RES)
+
+
+def test_pattern_constants_of_the_kernels():
+    # the constants in csrc/internal.h against their definitions: each pattern's
+    # period is the product of its primes (wheel bytes), each copy holds a period
+    # plus the largest segment plus 32 bytes rounded up to 16, and the first prime
+    # the small tier crosses is the base prime after the last pattern prime
+    import pathlib
+    import re
+    src = (pathlib.Path(__file__).resolve().parents[1] / "paper_1205_4883_gb300" / "csrc" / "internal.h").read_text()
+    const = {m.group(1): int(m.group(2)) for m in re.finditer(r"constexpr uint32_t (k\w+) = (\d+)u;", src)}
+    assert const["kTilePeriod"] == 7 * 11 * 13 * 17 * 19
+    assert const["kXTilePeriod0"] == 23 * 29 * 31
+    assert const["kXTilePeriod1"] == 37 * 41 * 43
+    assert const["kXTilePeriod2"] == 47 * 53 * 59
+    base = [2, 3, 5] + [p for p in range(7, 100) if all(p % d for d in range(2, int(p ** 0.5) + 1))]
+    assert base[const["kFirstCrossingPrime"]] == 23
+    assert base[const["kFirstCrossingPrimeX"]] == 61
+    seg = const["kMaxSegmentBytes"]
+    assert seg % 32 == 0 and seg + 3072 <= 227 * 1024
+    for per in (const["kXTilePeriod0"], const["kXTilePeriod1"], const["kXTilePeriod2"]):
+        stride = (per + seg + 32 + 15) & ~15
+        # the furthest 16-byte read of a segment starts below the period and stays in the copy
+        assert stride % 16 == 0 and ((per - 1) & ~15) + seg <= stride
