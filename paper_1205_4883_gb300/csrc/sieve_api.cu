@@ -3,10 +3,10 @@
 // include/gbsieve.h.
 //
 // Base primes (Section 1's sqrt bound) are made on the device in three
-// rounds, each using the sieve itself: primes < 256 by trial division, then
+// stages, each using the sieve itself: primes < 256 by trial division, then
 // primes <= min(limit, 65535) by sieving with those, then primes <= limit
 // (limit = floor(sqrt(hi_max - 1)) <= 2^31) by sieving with the primes below
-// 65536.  Every round's output is a list made by the compaction kernels.
+// 65536.  Every stage's output is a list made by the compaction kernels.
 
 #include <algorithm>
 #include <cmath>
@@ -609,7 +609,7 @@ int primes_upto(sieve_ctx *ctx, uint64_t limit, uint32_t **out_dev, std::vector<
 }
 
 int make_base_primes(sieve_ctx *ctx) {
-    // round 1: primes < 256 by trial division
+    // stage 1: primes < 256 by trial division
     uint32_t *d_tiny = nullptr, *d_ntiny = nullptr;
     int rc = dev_alloc(ctx, &d_tiny, 64);
     if (rc) return rc;
@@ -628,7 +628,7 @@ int make_base_primes(sieve_ctx *ctx) {
     if (rc) return rc;
     CK(launch_magic(ctx->d_primes, ctx->d_magic, ctx->h_primes.size(), ctx->stream));
 
-    // rounds 2 and 3
+    // stages 2 and 3
     const uint64_t stages[2] = {std::min<uint64_t>(ctx->prime_limit, 65535), ctx->prime_limit};
     for (int st = 0; st < 2; ++st) {
         const uint64_t lim = stages[st];
