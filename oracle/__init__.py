@@ -48,6 +48,8 @@ def _load():
         lib.oracle_bitmap.restype = u64
         lib.oracle_list.argtypes = [u64, u64, u64p, u64]
         lib.oracle_list.restype = u64
+        lib.oracle_crossings.argtypes = [u64, u64, u64, u64]
+        lib.oracle_crossings.restype = u64
         lib.oracle_default_threads.argtypes = []
         lib.oracle_default_threads.restype = ctypes.c_int
         _lib = lib
@@ -106,3 +108,9 @@ def primes(lo: int, hi: int) -> np.ndarray:
     m = _check(int(lib.oracle_list(lo, hi, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n)))
     assert m == n
     return out[:n]
+
+
+def crossings(lo: int, hi: int, pmin: int = 23, wheel: int = 30) -> int:
+    """Bit-clears of the crossing-off step on a wheel of modulus `wheel`: the
+    pairs (p, m), p prime >= pmin, m >= p, gcd(m, wheel) = 1, lo <= p m < hi."""
+    return _check(int(_load().oracle_crossings(lo, hi, pmin, wheel)))

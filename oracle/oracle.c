@@ -25,6 +25,9 @@
  *                    bits past the range in the last word are 0.  2 has no bit.
  *   list(lo, hi)   = the primes in [lo, hi) ascending, 2 included.
  * 0 and 1 are not prime.
+ *   crossings(lo, hi, pmin, w) = the bit-clears a wheel sieve of modulus w
+ *                    performs on [lo, hi) for the primes >= pmin (defined at
+ *                    oracle_crossings); the algorithmic work of the sieve.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -284,6 +287,70 @@ uint64_t oracle_list(uint64_t lo, uint64_t hi, uint64_t *out, uint64_t cap)
     }
     free(primes); free(mark);
     return n;
+}
+
+/* ---------------------------------------------------------------- crossing work */
+
+/* Greatest common divisor by Euclid's algorithm. */
+static uint64_t gcd_u64(uint64_t a, uint64_t b)
+{
+    while (b != 0) {
+        uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+/*
+ * #{ m : a <= m < b, gcd(m, w) = 1 }.  Every run of w consecutive integers
+ * holds phi(w) of them (phi = that count over 1..w); the integers left after
+ * the whole runs are tested one by one.
+ */
+static uint64_t coprime_between(uint64_t a, uint64_t b, uint64_t w, uint64_t phi)
+{
+    if (b <= a) return 0;
+    uint64_t runs = (b - a) / w;
+    uint64_t n = runs * phi;
+    for (uint64_t m = a + runs * w; m < b; ++m)
+        n += (gcd_u64(m, w) == 1);
+    return n;
+}
+
+/*
+ * The work of the crossing-off step on a wheel of modulus w.  Section 3.1
+ * marks the multiples of each prime; Section 1 limits the primes to those
+ * with p * p < hi; marking starts at p^2, i.e. at the multiple p * m with
+ * m = p.  A wheel of modulus w (30, 210; w = 1 for no wheel) has no place for
+ * integers sharing a factor with w, so only the multiples p * m with
+ * gcd(m, w) = 1 are marked there.  The result is the number of pairs (p, m)
+ * with p prime, pmin <= p, m >= p, gcd(m, w) = 1 and lo <= p * m < hi: one
+ * bit-clear each (a composite with several such prime factors is cleared
+ * once per factor).  Returns UINT64_MAX on failure (lo > hi, w = 0, no memory).
+ */
+uint64_t oracle_crossings(uint64_t lo, uint64_t hi, uint64_t pmin, uint64_t w)
+{
+    if (lo > hi || w == 0) return UINT64_MAX;
+    if (hi < 2) return 0;
+    uint64_t lim = oracle_isqrt(hi - 1); /* p * p < hi  <=>  p <= isqrt(hi - 1) */
+    uint64_t np = oracle_base_primes(lim, NULL, 0);
+    if (np == UINT64_MAX) return UINT64_MAX;
+    uint32_t *primes = (uint32_t *)malloc((np ? np : 1) * sizeof(uint32_t));
+    if (!primes) return UINT64_MAX;
+    oracle_base_primes(lim, primes, np);
+    uint64_t phi = 0;
+    for (uint64_t m = 1; m <= w; ++m) phi += (gcd_u64(m, w) == 1);
+    uint64_t total = 0;
+    for (uint64_t k = 0; k < np; ++k) {
+        uint64_t p = primes[k];
+        if (p < pmin) continue;
+        uint64_t m_lo = (lo + p - 1) / p;  /* smallest m with p * m >= lo */
+        if (m_lo < p) m_lo = p;            /* marking starts at p * p */
+        uint64_t m_hi = (hi - 1) / p + 1;  /* p * m < hi  <=>  m < m_hi */
+        total += coprime_between(m_lo, m_hi, w, phi);
+    }
+    free(primes);
+    return total;
 }
 
 /* Number of online cores the oracle uses when asked for "all of them". */
