@@ -114,7 +114,8 @@ int sieve_list64(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out_dev,
  * Compaction only: the ascending uint32 prime list of [lo, hi) read from an
  * odd-only bitmap of [lo, hi) that is already on the device (bitmap_dev,
  * layout above, e.g. written by sieve_bitmap).  Same *n / cap / ETRUNC
- * contract as sieve_list; requires hi <= 2^32.
+ * contract as sieve_list; requires hi <= 2^32.  For this call and the list
+ * calls, out_dev = NULL with cap > 0 is SIEVE_EINVAL, before any GPU work.
  */
 int sieve_compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo,
                   uint64_t hi, uint32_t *out_dev, size_t cap, uint64_t *n);
@@ -145,7 +146,10 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi,
  * words (the whole of [0, 2^32)); larger ranges, or hi > 2^32, return
  * SIEVE_ERANGE before any GPU work.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls on a device share the one array: calls that
+ * any stream capture.  The address is kept for the life of the process: do
+ * not call this function on a device after cudaDeviceReset of that device.
+ * out_dev = NULL with cap = 0 is the size query; NULL with cap > 0 is
+ * SIEVE_EINVAL, before any GPU work.  All calls on a device share the one array: calls that
  * overlap on the GPU (other streams or host threads) race, so serialise them.
  * The array keeps the last call's contents; every entry is written before it
  * is read, so nothing needs clearing.  Synchronous, like sieve_compact.
@@ -317,14 +321,48 @@ int sieve_selftest_wait(sieve_ctx *ctx, int arm, uint32_t limit, int *timed_out)
  */
 int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clears);
 
+/*
+ * As sieve_crossing_work, counting only the base primes p >= pmin (pmin <= 23
+ * gives sieve_crossing_work).  With pmin = 61 on the mod-30 wheel it is the
+ * clears left to the crossing loop's atomics after the further pre-sieved
+ * patterns of 23..59 (SIEVE_PARAM_PRESIEVE = 59) have made the others.
+ */
+int sieve_crossing_work_ge(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t pmin, uint64_t *clears);
+
+/*
+ * Roofline probes: what this GPU sustains for the operations the sieve's
+ * kernels are bound by, so that their rates can be set against a measured
+ * ceiling.  The paper has no counterpart (it reports no hardware rates).
+ * Runs on the context's stream and returns when done; *value receives:
+ *  - SIEVE_PROBE_SMEM_AND_CONFLICT_FREE: shared-memory atomicAnd, lane l of
+ *    every warp always on bank l, in lane-operations per SM clock (one CTA
+ *    of 1024 threads per SM, timed with clock64, so clock-independent);
+ *  - SIEVE_PROBE_SMEM_AND_RANDOM: the same on pseudo-random words (bank
+ *    conflicts as they fall), lane-operations per SM clock;
+ *  - SIEVE_PROBE_SMEM_STORE_CONFLICT_FREE: plain 32-bit stores, lane l on
+ *    bank l, lane-operations per SM clock;
+ *  - SIEVE_PROBE_HBM_WRITE: write-only HBM bandwidth in GB/s (10^9 B/s),
+ *    16-byte stores over buf_dev[0 .. bytes) (device memory of the caller,
+ *    16-byte aligned, at least 1 MiB; use more than the 129 MB L2), best of
+ *    five timed passes after a warm-up.
+ * buf_dev and bytes are ignored by the shared-memory probes.  The probes
+ * allocate a few bytes of device memory for their results.
+ */
+#define SIEVE_PROBE_SMEM_AND_CONFLICT_FREE   1
+#define SIEVE_PROBE_SMEM_AND_RANDOM          2
+#define SIEVE_PROBE_SMEM_STORE_CONFLICT_FREE 3
+#define SIEVE_PROBE_HBM_WRITE                4
+int sieve_probe(sieve_ctx *ctx, int kind, void *buf_dev, uint64_t bytes, double *value);
+
 /* The context's CUDA stream (a cudaStream_t) -- for event timing by callers. */
 void *sieve_stream(sieve_ctx *ctx);
 
 /* Static name of an error code. */
 const char *sieve_strerror(int code);
 
-/* The context's last error message ("" if none): a buffer of the context,
- * overwritten by its next failure. */
+/* The context's last error message ("" if none), copied under the context's
+ * lock into a buffer of the calling thread, valid until that thread's next
+ * call of this function (safe while a server runs on the context). */
 const char *sieve_last_error(sieve_ctx *ctx);
 
 #ifdef __cplusplus

@@ -42,6 +42,11 @@ SIEVE_PARAM_BATCH_ORDER = 13
 SIEVE_PARAM_FAULT_WAIT = 14
 SIEVE_PARAM_PRESIEVE = 15
 
+SIEVE_PROBE_SMEM_AND_CONFLICT_FREE = 1
+SIEVE_PROBE_SMEM_AND_RANDOM = 2
+SIEVE_PROBE_SMEM_STORE_CONFLICT_FREE = 3
+SIEVE_PROBE_HBM_WRITE = 4
+
 _u64 = ctypes.c_uint64
 _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -96,6 +101,7 @@ _SIGS = {
     "sieve_get_info": (_int, [_vp, ctypes.POINTER(sieve_info)]),
     "sieve_base_primes": (_int, [_vp, _pu32, _sz, _pu64]),
     "sieve_crossing_work": (_int, [_vp, _u64, _u64, _pu64]),
+    "sieve_crossing_work_ge": (_int, [_vp, _u64, _u64, _u64, _pu64]),
     "sieve_stream": (_vp, [_vp]),
     "sieve_strerror": (ctypes.c_char_p, [_int]),
     "sieve_last_error": (ctypes.c_char_p, [_vp]),
@@ -107,6 +113,7 @@ _SIGS = {
     "sieve_server_stats": (_int, [_vp, ctypes.POINTER(sieve_server_counters)]),
     "sieve_server_destroy": (None, [_vp]),
     "sieve_selftest_wait": (_int, [_vp, _int, ctypes.c_uint32, ctypes.POINTER(_int)]),
+    "sieve_probe": (_int, [_vp, _int, _vp, _u64, ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -250,6 +257,15 @@ def sieve_selftest_wait(ctx: int, arm: bool, limit: int) -> bool:
     return bool(out.value)
 
 
+def sieve_probe(ctx: int, kind: int, buf=None, nbytes: int = 0) -> float:
+    """A roofline probe (SIEVE_PROBE_*): lane-ops per SM clock, or GB/s for the HBM write."""
+    v = ctypes.c_double()
+    if buf is not None and not isinstance(buf, int) and not nbytes:
+        nbytes = buf.numel() * buf.element_size()
+    _check(ctx, load_library().sieve_probe(ctx, kind, _ptr(buf), nbytes, ctypes.byref(v)))
+    return v.value
+
+
 def sieve_batch_count(ctx: int, lo: Sequence[int], hi: Sequence[int], bitmaps=None):
     """Counts of m ranges in one launch; `bitmaps` optionally a list of CUDA tensors (or None)."""
     import numpy as np
@@ -297,6 +313,12 @@ def sieve_base_primes(ctx: int):
 def sieve_crossing_work(ctx: int, lo: int, hi: int) -> int:
     c = _u64()
     _check(ctx, load_library().sieve_crossing_work(ctx, lo, hi, ctypes.byref(c)))
+    return c.value
+
+
+def sieve_crossing_work_ge(ctx: int, lo: int, hi: int, pmin: int) -> int:
+    c = _u64()
+    _check(ctx, load_library().sieve_crossing_work_ge(ctx, lo, hi, pmin, ctypes.byref(c)))
     return c.value
 
 
@@ -500,8 +522,10 @@ class Sieve:
     def base_primes(self):
         return sieve_base_primes(self.ctx)
 
-    def crossing_work(self, lo, hi):
-        return sieve_crossing_work(self.ctx, lo, hi)
+    def crossing_work(self, lo, hi, pmin=None):
+        if pmin is None:
+            return sieve_crossing_work(self.ctx, lo, hi)
+        return sieve_crossing_work_ge(self.ctx, lo, hi, pmin)
 
     def stream(self):
         return sieve_stream(self.ctx)

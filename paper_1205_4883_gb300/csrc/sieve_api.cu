@@ -488,6 +488,7 @@ int launch_ranges210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, Lau
 
 int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
                  uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64) {
+    if (!out_dev && cap) return fail(ctx, SIEVE_EINVAL, "null output with a nonzero capacity");
     const uint64_t nwords = bitmap_words_of(lo, hi);
     const uint32_t two = (lo <= 2 && 2 < hi) ? 1 : 0;
     const uint64_t ntiles = (nwords + kCompactTileWords - 1) / kCompactTileWords;
@@ -745,7 +746,16 @@ const char *sieve_strerror(int code) {
     return kNames[i];
 }
 
-const char *sieve_last_error(sieve_ctx *ctx) { return ctx ? ctx->last_error : ""; }
+const char *sieve_last_error(sieve_ctx *ctx) {
+    // the context's buffer may be rewritten by a server thread at any time: hand out a
+    // copy taken under the lock, in a buffer of the calling thread
+    static thread_local char copy[sizeof(sieve_ctx::last_error)];
+    if (!ctx) return "";
+    std::lock_guard<std::mutex> lk(ctx->err_mu);
+    std::memcpy(copy, ctx->last_error, sizeof copy);
+    copy[sizeof copy - 1] = 0;
+    return copy;
+}
 
 uint64_t sieve_bitmap_words(uint64_t lo, uint64_t hi) { return lo > hi ? 0 : bitmap_words_of(lo, hi); }
 
@@ -1130,12 +1140,12 @@ int sieve_selftest_wait(sieve_ctx *ctx, int arm, uint32_t limit, int *timed_out)
     return SIEVE_OK;
 }
 
-int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clears) {
+int sieve_crossing_work_ge(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t pmin, uint64_t *clears) {
     if (!clears) return fail(ctx, SIEVE_EINVAL, "null clears");
     int rc = check_range(ctx, lo, hi);
     if (rc) return rc;
-    // For each base prime p >= 23: #{ m : m >= p, gcd(m, W) = 1, lo <= p m < hi }, W the
-    // wheel of the count path (30, or 210 when SIEVE_PARAM_WHEEL is 210).
+    // For each base prime p >= max(pmin, 23): #{ m : m >= p, gcd(m, W) = 1, lo <= p m < hi },
+    // W the wheel of the count path (30, or 210 when SIEVE_PARAM_WHEEL is 210).
     const uint64_t W = ctx->params.wheel == 210 ? 210 : 30;
     uint64_t cum[211] = {0};  // cum[r] = #{ 1 <= m < r : gcd(m, W) = 1 }
     for (uint64_t r = 1; r <= W; ++r) cum[r] = cum[r - 1] + ((r - 1) % 2 && (r - 1) % 3 && (r - 1) % 5 && (W == 30 || (r - 1) % 7));
@@ -1146,12 +1156,17 @@ int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clea
     const uint32_t n_use = primes_needed(ctx, hi);
     for (uint32_t i = kFirstCrossingPrime; i < n_use; ++i) {
         const uint64_t p = ctx->h_primes[i];
+        if (p < pmin) continue;
         uint64_t m_lo = std::max<uint64_t>(p, (lo + p - 1) / p);
         uint64_t m_hi = (hi + p - 1) / p;  // m < m_hi  <=>  p m < hi
         if (m_hi > m_lo) total += coprime_below(m_hi) - coprime_below(m_lo);
     }
     *clears = total;
     return SIEVE_OK;
+}
+
+int sieve_crossing_work(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *clears) {
+    return sieve_crossing_work_ge(ctx, lo, hi, 23, clears);
 }
 
 }  // extern "C"

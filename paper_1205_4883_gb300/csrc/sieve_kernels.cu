@@ -597,7 +597,13 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                 tile_phase ^= 1u;
             }
             __syncthreads();
-            if (s_tile_fail) break;  // every thread sees it after the barrier
+            // Every thread sees a failed wait after the barrier, and the CTA stops.  Its bulk
+            // copy may then still be outstanding: the CTA exits without waiting for it (a
+            // wait that already ran out for 2^24 polls would not end), which is only sound
+            // because the copy is taken never to complete.  The host turns the flag into
+            // SIEVE_EDEVICE and trusts no output of this launch; the condition has never
+            // been seen in normal runs.
+            if (s_tile_fail) break;
             // 1'. the further patterns (primes 23..59), ANDed in 16 bytes at a time
             //     from their L2-resident shifted copies
             if (P.xtile0) {

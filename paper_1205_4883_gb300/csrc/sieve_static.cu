@@ -59,12 +59,16 @@ cudaError_t scratch_on_current_device(unsigned char **out) {
 
 extern "C" int sieve_compact_static(const uint32_t *bitmap_dev, uint64_t lo, uint64_t hi, uint32_t *out_dev,
                                     size_t cap, uint64_t *n, void *cuda_stream) {
+    // argument checks in sieve_compact's order, all before any GPU work
     if (!n || lo > hi) return SIEVE_EINVAL;
     if (hi > (1ull << 32)) return SIEVE_ERANGE;
     const uint64_t o0 = lo | 1;
     const uint64_t nwords = o0 < hi ? ((hi - o0 + 1) / 2 + 31) / 32 : 0;
-    if (nwords > SIEVE_STATIC_MAX_WORDS) return SIEVE_ERANGE;
     if (nwords && !bitmap_dev) return SIEVE_EINVAL;
+    if (!out_dev && cap) return SIEVE_EINVAL;
+    // with hi <= 2^32 the bitmap has at most 2^26 words, so this cannot fire today; it
+    // keeps the scratch array safe should SIEVE_STATIC_MAX_WORDS ever be made smaller
+    if (nwords > SIEVE_STATIC_MAX_WORDS) return SIEVE_ERANGE;
     const uint32_t two = (lo <= 2 && 2 < hi) ? 1 : 0;
     const uint64_t ntiles = (nwords + kCompactTileWords - 1) / kCompactTileWords;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);

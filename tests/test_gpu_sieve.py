@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+import oracle_pool
 from numtheory import load_golden, mr_is_prime, td_is_prime
 
 pytestmark = pytest.mark.gpu
@@ -250,6 +251,8 @@ def test_pi_1e12_full_size(sv):
 
 
 def test_range_2p32_bitmap_then_compaction(sv):
+    # the [0, 2^32) workload at full size in the bench's launch shape (sieve_bitmap, then
+    # sieve_compact): every word of the bitmap and every entry of the list against the oracle
     lo, hi = 0, 1 << 32
     nw = gb.sieve_bitmap_words(lo, hi)
     assert nw == 1 << 26
@@ -259,37 +262,63 @@ def test_range_2p32_bitmap_then_compaction(sv):
     lst = torch.empty(PI[1 << 32], dtype=torch.int32, device="cuda")
     n, rc = gb.sieve_compact(sv.ctx, bm, lo, hi, lst)
     assert rc == gb.SIEVE_OK and n == PI[1 << 32]
-    # properties that hold at any size
-    u = lst.to(torch.int64) & 0xFFFFFFFF
-    assert bool((u[1:] > u[:-1]).all().item())
-    assert int(u[0].item()) == 2 and int(u[-1].item()) == 4_294_967_291
-    # sampled windows against the oracle
-    rng = np.random.default_rng(5)
     bmh = bm.cpu().numpy().view(np.uint32)
-    for w in rng.integers(0, nw - 1024, 12):
-        a = 64 * int(w)
-        assert np.array_equal(bmh[w:w + 1024], oracle.bitmap(a, a + 64 * 1024)), w
-    uh = u.cpu().numpy()
-    for k in list(rng.integers(0, n - 2000, 4)) + [n - 2000]:
-        k = int(k)
-        window = uh[k:k + 2000].astype(np.uint64)
-        assert np.array_equal(window, oracle.primes(int(window[0]), int(window[-1]) + 1))
-        assert oracle.count(0, int(window[0])) == k  # the rank of the window's first prime
+    assert oracle_pool.compare_bitmap(bmh, lo, hi) == []
+    uh = lst.cpu().numpy().view(np.uint32)
+    total, bad = oracle_pool.compare_list(uh, lo, hi)
+    assert total == n and bad == []
+    assert int(uh[0]) == 2 and int(uh[-1]) == 4_294_967_291
 
 
 def test_batch_4096_intervals(sv):
+    # the batched workload at full size: every one of the 4096 counts against the oracle,
+    # and against the single-range call on the same GPU for a sample
     los, his = batch_intervals(4096, seed=1205)
     counts = sv.batch_count(los, his)
-    # each count equals the single-range call on the same GPU (exact)
-    for i in range(0, 4096, 37):
+    assert counts == oracle_pool.counts(los, his)
+    for i in range(0, 4096, 97):
         assert counts[i] == sv.count(los[i], his[i]), i
-    # and a seeded sample against the oracle: the narrowest intervals plus random ones
-    order = np.argsort(np.array(his, dtype=np.float64) - np.array(los, dtype=np.float64))
-    sample = list(order[:24]) + list(np.random.default_rng(1).choice(4096, 16, replace=False))
-    for i in sample:
-        i = int(i)
-        if his[i] - los[i] <= 3 * 10**7:
-            assert counts[i] == oracle.count(los[i], his[i]), i
+
+
+def test_batch_4096_intervals_with_bitmaps(sv):
+    # the same 4096 intervals with a bitmap for every one, in one launch (bitmap mode):
+    # each count and every word of each bitmap against the oracle
+    los, his = batch_intervals(4096, seed=1205)
+    nws = [gb.sieve_bitmap_words(a, b) for a, b in zip(los, his)]
+    offs = np.concatenate([[0], np.cumsum(nws)]).astype(np.int64)
+    store = torch.zeros(int(offs[-1]) + 1, dtype=torch.int32, device="cuda")
+    base = store.data_ptr()
+    ptrs = [base + 4 * int(offs[i]) for i in range(4096)]
+    counts = sv.batch_count(los, his, ptrs)
+    host = store.cpu().numpy().view(np.uint32)
+
+    def check(i):
+        ref = oracle.bitmap(los[i], his[i])
+        ok = np.array_equal(host[offs[i]:offs[i + 1]], ref)
+        return ok and counts[i] == int(np.unpackbits(ref.view(np.uint8)).sum()) + (los[i] <= 2 < his[i])
+
+    bad = [i for i, ok in zip(range(4096), oracle_pool.pmap(check, range(4096))) if not ok]
+    assert bad == []
+
+
+def test_crossing_work_matches_the_oracle(sv):
+    # the roofline numerator (sieve_crossing_work, host arithmetic in the library) against
+    # the oracle's count of the same bit-clears: the stored golden values at full size,
+    # then random ranges
+    for lo, hi, pmin, w, v in load_golden("crossings.txt"):
+        lo, hi, pmin, w, v = (int(x) for x in (lo, hi, pmin, w, v))
+        if hi > HI_MAX:
+            continue
+        sv.set_param(gb.SIEVE_PARAM_WHEEL, w)
+        try:
+            assert sv.crossing_work(lo, hi, pmin) == v, (lo, hi, pmin, w)
+            if pmin == 23:
+                assert sv.crossing_work(lo, hi) == v
+        finally:
+            sv.set_param(gb.SIEVE_PARAM_WHEEL, 30)
+    for lo, hi in random_ranges(20, seed=31, max_lo=10**14, max_w=10**9):
+        for pmin in (23, 61, 1000):
+            assert sv.crossing_work(lo, hi, pmin) == oracle.crossings(lo, hi, max(pmin, 23), 30), (lo, hi)
 
 
 def test_batch_order_does_not_change_results(sv):
