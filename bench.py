@@ -1,8 +1,12 @@
 """Throughput of the segmented sieve on GB300: integers sieved per second.
 
 Default workload: count the primes in [0, 10^12) (pi(10^12) = 37607912018)
-in one range, count-only, mod-30 wheel with the pre-sieved pattern.  Prints
-one JSON line (rank 0).
+in one range, count-only, mod-30 wheel with the pre-sieved patterns.  Prints
+one JSON line (rank 0).  At one GPU the line also carries the batched
+(4096 intervals, one launch) and served (a Poisson request stream) workloads
+as sub-objects, each against the plain single-range sieve of the same number
+of integers on the same GPU (the speedup S of the paper's Eq. 1), with its own
+clock record, roofline and CPU-oracle baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbsieve|reference]
 
@@ -11,10 +15,9 @@ With N > 1 (torchrun, one rank per GPU) each rank sieves its own block of
 on the data path (weak scaling).  --impl reference times the CPU oracle on
 the host cores on a bounded sample of the same workload.
 
-Other workloads (one GPU, one JSON line each): --workload batched (4096
-intervals, one launch), served (a Poisson request stream through the
-server), range2p32 (odd-only bitmap and u32 list of [0, 2^32)) and pi1e7
-(count, bitmap and list of [0, 10^7)).
+Other workloads (one GPU, one JSON line each): --workload batched, served,
+range2p32 (odd-only bitmap and u32 list of [0, 2^32)), pi1e7 (count, bitmap
+and list of [0, 10^7)) and peaks (the roofline probes alone).
 """
 from __future__ import annotations
 
@@ -53,6 +56,21 @@ def _traffic():
     except OSError:
         return None
     return TRAFFIC["bytes"] if sha == TRAFFIC["kernel_sha256_16"] else None
+
+
+def _published_pi():
+    """Published values of pi(x) (OEIS A006880, A007053) from the test fixtures, to
+    check the timed result against a value that does not come from the GPU."""
+    out = {}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "pi_values.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 2 and not line.startswith("#"):
+                    out[int(parts[0])] = int(parts[1])
+    except OSError:
+        pass
+    return out
 
 
 def _peaks():
@@ -217,6 +235,9 @@ def run_gpu(args):
         sv.count_dev(lo, hi, out)
     torch.cuda.synchronize()
     expect = sv.count(lo, hi)
+    published = _published_pi()
+    if lo == 0 and hi in published and expect != published[hi]:  # pi(10^12), OEIS A006880
+        raise RuntimeError(f"count of [0, {hi}) is {expect}, the published pi({hi}) is {published[hi]}")
 
     props = torch.cuda.get_device_properties(dev)
     gpu_id = _gpu_id(dev)
@@ -258,10 +279,12 @@ def run_gpu(args):
     peaks, peak_kind = _peaks()
     clocks = clk.summary()
     n_sms = props.multi_processor_count
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    clears = sv.crossing_work(lo, hi)
-    peak_ops = n_sms * 32 * sm_max * 1e6  # one shared-memory op per lane per clock
-    achieved = clears / (ms_step * 1e-3)
+    clears = sv.crossing_work(lo, hi)          # the method's bit-clears (primes >= 23)
+    atomics = sv.crossing_work(lo, hi, 61)     # those the kernel makes as atomics (primes >= 61)
+    probes = _probe_rates(sv) if ws == 1 else None
+    roof = _op_roofline(clears, ms_step * 1e-3, n_sms, peaks, peak_kind,
+                        probes["smem_and_conflict_free_lanes_per_clk_sm"] if probes else None, atomics)
+    roof["traffic"] = _traffic() if args.hi is None and ws == 1 else None
     line = None
     if rank == 0:
         line = {
@@ -276,12 +299,8 @@ def run_gpu(args):
                        "ctas_per_sm": sv.get_param(gb.SIEVE_PARAM_CTAS_PER_SM),
                        "l2": "flushed between steps (256 MiB write, untimed)",
                        "parallelism": f"{ws} independent ranges" if ws > 1 else "1 range"},
-            "roofline": {"bound": "alu", "op": "shared-memory bit-clear (atom.shared.and)",
-                         "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
-                         "frac": achieved / peak_ops,
-                         "traffic": _traffic() if args.hi is None and ws == 1 else None,
-                         "peak_basis": f"{n_sms} SMs x 32 lanes/clk x {sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
-                         "work_per_launch": clears},
+            "roofline": roof,
+            "probes": probes,
             "clocks": clocks,
             "e2e": {"value": ws * units / e2e_s, "unit": METRIC, "h2d_bytes_per_step": 72,
                     "d2h_bytes_per_step": 8},
@@ -301,58 +320,205 @@ def _gpu_id(dev):
     return f"GPU-{u}" if u is not None and not str(u).startswith("GPU-") else str(u or dev)
 
 
-def _event_ms(fn, reps):
+def _event_ms(fn, reps, stream=None):
+    """Mean CUDA-event time of fn() over reps calls (after one untimed call)."""
     import torch
+    stream = stream or torch.cuda.current_stream()
+    fn()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    a.record()
+    a.record(stream)
     for _ in range(reps):
         fn()
-    b.record()
+    b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
 
 
-def run_batched(args):
+def _op_roofline(clears, seconds, n_sms, peaks, peak_kind, probe=None, atomics=None):
+    """Shared-memory bit-clear roofline: the method's clears per second against the
+    nominal op peak (one lane-op per lane per SM clock); with the measured probe
+    rate (lane-ops per SM clock) and the clears the kernel makes as atomics."""
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = n_sms * 32 * sm_max * 1e6
+    achieved = clears / seconds
+    out = {"bound": "alu", "op": "shared-memory bit-clear (atom.shared.and)", "achieved": achieved / 1e9,
+           "peak": peak_ops / 1e9, "unit": "Gop/s", "frac": achieved / peak_ops,
+           "peak_basis": f"{n_sms} SMs x 32 lanes/clk x {sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
+           "work_per_launch": clears}
+    if probe:
+        mp = n_sms * probe * sm_max * 1e6
+        out["peak_probe"] = {"value": mp / 1e9, "unit": "Gop/s", "frac": achieved / mp,
+                             "basis": f"conflict-free atomicAnd probe, {probe:.2f} lane-ops/clk/SM x {n_sms} SMs "
+                                      f"x {sm_max:.0f} MHz"}
+    if atomics is not None:
+        out["atomics_per_launch"] = atomics
+        out["frac_atomics"] = atomics / seconds / peak_ops
+        if probe:
+            out["frac_atomics_of_probe"] = atomics / seconds / (n_sms * probe * sm_max * 1e6)
+    return out
+
+
+def _probe_rates(sv):
+    """Measured roofline denominators (sieve_probe): shared-memory lane-ops per SM clock
+    and write-only HBM GB/s."""
+    import torch
+    import paper_1205_4883_gb300 as gb
+    out = {
+        "smem_and_conflict_free_lanes_per_clk_sm": gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_CONFLICT_FREE),
+        "smem_and_random_lanes_per_clk_sm": gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_RANDOM),
+        "smem_store_conflict_free_lanes_per_clk_sm": gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_STORE_CONFLICT_FREE),
+    }
+    buf = torch.empty(2 << 30, dtype=torch.uint8, device="cuda")
+    out["hbm_write_gbs"] = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_HBM_WRITE, buf)
+    del buf
+    return out
+
+
+def _cpu_intervals(items, budget_s=12.0):
+    """The oracle (unchanged) on the host cores over a bounded prefix of the given
+    (lo, hi, kind) items, one oracle call per item on a thread pool (ctypes
+    releases the GIL): count for a count item, the list for a list item.  Items
+    are taken in a fixed order until about budget_s seconds are spent."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    oracle.build()
+    cores = oracle.default_threads()
+
+    def one(it):
+        lo, hi, kind = it
+        if kind == "list":
+            return len(oracle.primes(lo, hi))
+        return oracle.count(lo, hi, 1)
+
+    done, ints, t0 = 0, 0, time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        while done < len(items) and time.perf_counter() - t0 < budget_s:
+            chunk = items[done:done + 4 * cores]
+            list(ex.map(one, chunk))
+            done += len(chunk)
+            ints += sum(h - l for l, h, _ in chunk)
+    dt = time.perf_counter() - t0
+    return {"value": ints / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"first {done} of {len(items)} items ({ints} integers) on {cores} threads, {dt:.2f} s"}
+
+
+def _plain_same_integers(sv, lo, n, reps=3):
+    """The plain single-range sieve (count_dev, one launch) of n integers from lo on the
+    same GPU: the T_serial of Eq. 1's speedup for a workload of n integers."""
+    import torch
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ms = _event_ms(lambda: sv.count_dev(lo, lo + n, out), reps, torch.cuda.current_stream())
+    return {"value": n / (ms * 1e-3), "unit": METRIC, "range": [lo, lo + n], "ms": ms}
+
+
+def batched_measure(steps=10, warmup=3, cpu=True, tuned=True):
     """4096 intervals from seed 1205, lo log-uniform in [10^6, 10^14], width log-uniform in
-    [10^3, 10^8]: one graph-replayed persistent launch per step; compared with sieving the
-    same intervals one call at a time and with the plain single-range rate."""
+    [10^3, 10^8]: one graph-replayed persistent launch per call (sieve_batch_count, host
+    arrays in, host counts out).  Compared with the plain single-range sieve of the same
+    number of integers at the batch's median start, and with one call per interval."""
     import torch
     import paper_1205_4883_gb300 as gb
     from paper_1205_4883_gb300.workloads import batch_intervals
-    torch.cuda.set_device(0)
     los, his = batch_intervals(4096, seed=1205)
     units = sum(h - l for l, h in zip(los, his))
     sv = gb.Sieve(max(max(his), 10**14 + 10**10))
     ref = sv.batch_count(los, his)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         sv.batch_count(los, his)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        got = sv.batch_count(los, his)
-    dt = (time.perf_counter() - t0) / args.steps
-    assert got == ref
+    torch.cuda.synchronize()
+    with ClockSampler(_gpu_id(torch.cuda.current_device())) as clk:
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            got = sv.batch_count(los, his)
+        dt = (time.perf_counter() - t0) / steps
+    if got != ref:
+        raise RuntimeError("batched counts changed between calls")
     t0 = time.perf_counter()
     for lo, hi in zip(los, his):
         sv.count(lo, hi)
     one_by_one = time.perf_counter() - t0
-    out = torch.zeros(1, dtype=torch.int64, device="cuda")
-    plain_ms = _event_ms(lambda: sv.count_dev(10**14, 10**14 + 10**10, out), 3)
-    line = {"metric": METRIC, "value": units / dt, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "batched: 4096 intervals, seed 1205, lo log-uniform [1e6, 1e14], "
-                                   "w log-uniform [1e3, 1e8], counts, one graph replay per step",
-                       "integers": units},
-            "one_call_per_interval": {"value": units / one_by_one, "unit": METRIC},
-            "plain_single_range": {"value": 10**10 / (plain_ms * 1e-3), "unit": METRIC,
-                                   "range": "[1e14, 1e14 + 1e10)"}}
+    med = sorted(los)[len(los) // 2]
+    plain = _plain_same_integers(sv, med, units)
+    peaks, peak_kind = _peaks()
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    clears = sum(sv.crossing_work(l, h) for l, h in zip(los, his))
+    atomics = sum(sv.crossing_work(l, h, 61) for l, h in zip(los, his))
+    probe = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_CONFLICT_FREE)
+    out = {"value": units / dt, "unit": METRIC, "ms_per_step": dt * 1e3, "steps": steps, "warmup": warmup,
+           "config": {"workload": "batched: 4096 intervals, seed 1205, lo log-uniform [1e6, 1e14], "
+                                  "w log-uniform [1e3, 1e8], counts, one graph replay per call",
+                      "integers": units, "timing": "host wall clock around sieve_batch_count "
+                                                   "(host arrays in, host counts out)"},
+           "vs_plain": (units / dt) / plain["value"],
+           "plain_single_range": plain,
+           "one_call_per_interval": {"value": units / one_by_one, "unit": METRIC},
+           "roofline": _op_roofline(clears, dt, n_sms, peaks, peak_kind, probe, atomics),
+           "clocks": clk.summary()}
+    if tuned:
+        from paper_1205_4883_gb300 import autotune
+        table = autotune.load_table()
+        if table.get("classes"):
+            tref = sv.batch_count_tuned(los, his, table)
+            if tref != ref:
+                raise RuntimeError("tuned batch differs from the untuned one")
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                sv.batch_count_tuned(los, his, table)
+            tdt = (time.perf_counter() - t0) / steps
+            out["tuned"] = {"value": units / tdt, "unit": METRIC, "ms_per_step": tdt * 1e3,
+                            "vs_untuned": dt / tdt}
     sv.close()
+    if cpu:
+        order = list(range(4096))
+        out["cpu_baseline"] = _cpu_intervals([(los[i], his[i], "count") for i in order])
+    return out
+
+
+def run_batched(args):
+    out = batched_measure(args.steps, args.warmup)
+    line = {"metric": METRIC, "value": out["value"], "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": out["config"]}
+    line.update({k: v for k, v in out.items() if k not in line})
     print(json.dumps(line))
     return 0
 
 
-def run_outputs(args, lo, hi, name, with_count):
+def _cpu_outputs(lo, hi, with_count, budget_s=12.0):
+    """The oracle (unchanged) producing the same outputs (count if asked, odd-only bitmap,
+    prime list) of [lo, hi) on the host cores: windows of 2^26 integers on a thread pool
+    (ctypes releases the GIL), taken in order until about budget_s seconds are spent."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    oracle.build()
+    cores = oracle.default_threads()
+    step = 1 << 26
+    edges = list(range(lo, hi, step)) + [hi]
+    spans = list(zip(edges[:-1], edges[1:]))
+
+    def one(ab):
+        a, b = ab
+        if with_count:
+            oracle.count(a, b, 1)
+        oracle.bitmap(a, b)
+        return len(oracle.primes(a, b))
+
+    done, ints, t0 = 0, 0, time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        while done < len(spans) and time.perf_counter() - t0 < budget_s:
+            chunk = spans[done:done + 2 * cores]
+            list(ex.map(one, chunk))
+            done += len(chunk)
+            ints += sum(b - a for a, b in chunk)
+    dt = time.perf_counter() - t0
+    return {"value": ints / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{'count, ' if with_count else ''}bitmap and list of {done} of {len(spans)} windows of "
+                      f"2^26 integers ({ints} integers) on {cores} threads, {dt:.2f} s"}
+
+
+def outputs_measure(lo, hi, name, with_count, steps=10, warmup=3, cpu=True):
     """One range's outputs through the C ABI into preallocated device buffers: (optionally the
     count,) the odd-only bitmap (sieve_bitmap) and the prime list compacted from it
     (sieve_compact, u32).  Per stage: CUDA-event time on the context's stream.  The bitmap
@@ -366,6 +532,9 @@ def run_outputs(args, lo, hi, name, with_count):
     stream = torch.cuda.current_stream()
     nw = gb.sieve_bitmap_words(lo, hi)
     n = sv.count(lo, hi)
+    published = _published_pi()
+    if lo == 0 and hi in published and n != published[hi]:
+        raise RuntimeError(f"count of [0, {hi}) is {n}, the published pi({hi}) is {published[hi]}")
     bm = torch.empty(nw, dtype=torch.int32, device="cuda")
     lst = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
     host = torch.empty(max(n, 1), dtype=torch.int32, pin_memory=True)
@@ -381,149 +550,202 @@ def run_outputs(args, lo, hi, name, with_count):
         evs[2].record(stream)
         return c, k
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         stages([torch.cuda.Event(enable_timing=True) for _ in range(3)])
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
     with ClockSampler(_gpu_id(torch.cuda.current_device())) as clk:
-        for k in range(args.steps):
+        for k in range(steps):
             flush.zero_()
             c, got = stages(evs[k])
         torch.cuda.synchronize()
     assert c == n and got == n
-    t_bm = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
-    t_ls = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    t_bm = sum(e[0].elapsed_time(e[1]) for e in evs) / steps
+    t_ls = sum(e[1].elapsed_time(e[2]) for e in evs) / steps
     # end to end: count (if asked), bitmap, list, and the list copied to pinned host memory
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         stages([torch.cuda.Event(enable_timing=True) for _ in range(3)])
         host.copy_(lst, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = (time.perf_counter() - t0) / steps
     peaks, peak_kind = _peaks()
-    props = torch.cuda.get_device_properties(0)
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak_ops = props.multi_processor_count * 32 * sm_max * 1e6
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
     clears = sv.crossing_work(lo, hi)
+    atomics = sv.crossing_work(lo, hi, 61)
+    probe = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_CONFLICT_FREE)
+    wbuf = torch.empty(2 << 30, dtype=torch.uint8, device="cuda")
+    hbm_write = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_HBM_WRITE, wbuf)
+    del wbuf
     list_bytes = 4 * n + 4 * nw  # the list written, the bitmap read once (a second read is not credited)
     hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
-    bm_line = {"bound": "alu", "op": "shared-memory bit-clear (atom.shared.and)", "kernel": "k_sieve<1>",
-               "achieved": clears / (t_bm * 1e-3) / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
-               "frac": clears / (t_bm * 1e-3) / peak_ops, "traffic": None, "work_per_launch": clears,
-               "bitmap_bytes_written": 4 * nw}
+    bm_line = _op_roofline(clears, t_bm * 1e-3, n_sms, peaks, peak_kind, probe, atomics)
+    bm_line.update({"kernel": "k_sieve<1>", "traffic": None, "bitmap_bytes_written": 4 * nw})
     ls_line = {"bound": "hbm", "kernel": "k_tile_popc + k_tile_scan + k_emit (sieve_compact)",
                "achieved": list_bytes / (t_ls * 1e-3) / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
                "frac": list_bytes / (t_ls * 1e-3) / hbm, "traffic": None, "bytes_per_call": list_bytes,
-               "peak_basis": f"{peak_kind} hbm_gbs (copy, read + write)"}
+               "peak_basis": f"{peak_kind} hbm_gbs (copy, read + write)",
+               "peak_write_probe": {"value": hbm_write, "unit": "GB/s",
+                                    "frac": list_bytes / (t_ls * 1e-3) / (hbm_write * 1e9),
+                                    "basis": "write-only HBM probe (sieve_probe), 2 GiB of 16-byte stores"}}
     dominant = bm_line if t_bm >= t_ls else ls_line
-    line = {"metric": METRIC, "value": (hi - lo) / ((t_bm + t_ls) * 1e-3), "unit": METRIC, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_bm + t_ls, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": name, "lo": lo, "hi": hi, "primes": n, "bitmap_words": nw,
-                       "l2": "flushed between steps (256 MiB write, untimed); outputs larger than L2"},
-            "stages_ms": {"bitmap": t_bm, "list": t_ls},
-            "roofline": dominant, "roofline_list": ls_line, "roofline_bitmap": bm_line,
-            "clocks": clk.summary(),
-            "e2e": {"value": (hi - lo) / e2e_s, "unit": METRIC, "h2d_bytes_per_step": 72,
-                    "d2h_bytes_per_step": 4 * n + 8},
-            "gpu_launches": args.steps * 5}
+    out = {"value": (hi - lo) / ((t_bm + t_ls) * 1e-3), "unit": METRIC, "ms_per_step": t_bm + t_ls,
+           "steps": steps, "warmup": warmup,
+           "config": {"workload": name, "lo": lo, "hi": hi, "primes": n, "bitmap_words": nw,
+                      "l2": "flushed between steps (256 MiB write, untimed)"},
+           "stages_ms": {"bitmap": t_bm, "list": t_ls},
+           "roofline": dominant, "roofline_list": ls_line, "roofline_bitmap": bm_line,
+           "clocks": clk.summary(),
+           "e2e": {"value": (hi - lo) / e2e_s, "unit": METRIC, "h2d_bytes_per_step": 72,
+                   "d2h_bytes_per_step": 4 * n + 8}}
     sv.close()
+    del bm, lst, host, flush
+    if cpu:
+        out["cpu_baseline"] = _cpu_outputs(lo, hi, with_count)
+    return out
+
+
+def run_outputs(args, lo, hi, name, with_count):
+    out = outputs_measure(lo, hi, name, with_count, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+    line = {"metric": METRIC, "value": out["value"], "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": out["config"],
+            "gpu_launches": args.steps * 5}
+    line.update({k: v for k, v in out.items() if k not in line})
     print(json.dumps(line))
     return 0
 
 
-def run_served(args):
+def served_measure(rates, requests=0, cpu=True):
     """A seeded Poisson stream (80% count, 20% list; lo log-uniform in [0, 1e12], width
-    log-uniform in [1e4, 1e9]) at each offered rate: p50/p99 latency and integers/s."""
+    log-uniform in [1e4, 1e9]) at each offered rate through the request server:
+    p50/p99 latency (submit to result on the host) and integers/s, against the plain
+    single-range sieve of the same number of integers at the stream's median start."""
+    import queue
+    import threading
+
     import numpy as np
     import torch
     import paper_1205_4883_gb300 as gb
     from paper_1205_4883_gb300.workloads import served_stream
-    torch.cuda.set_device(0)
     sv = gb.Sieve(10**12 + 10**9 + 1)
-    out = torch.zeros(1, dtype=torch.int64, device="cuda")
-    plain_ms = _event_ms(lambda: sv.count_dev(0, 10**11, out), 2)
-    rates = [float(r) for r in args.rates.split(",")]
-    results = []
-    for rate in rates:
-        n = args.requests or int(min(10000, max(300, rate)))
-        reqs = served_stream(rate=rate, n=n, seed=1205)
-        with gb.Server(sv, max_device_bytes=16 << 30) as srv:
-            import queue
-            import threading
-            tickets = queue.Queue()
-            lat = []
-            errors = []
+    results, all_reqs = [], []
+    with ClockSampler(_gpu_id(torch.cuda.current_device())) as clk:
+        for rate in rates:
+            n = requests or int(min(10000, max(300, rate)))
+            reqs = served_stream(rate=rate, n=n, seed=1205)
+            all_reqs.append(reqs)
+            with gb.Server(sv, max_device_bytes=16 << 30) as srv:
+                tickets = queue.Queue()
+                lat, errors = [], []
 
-            def collect():  # picks up finished results in any order and releases them (frees slots)
-                outstanding, closed = [], False
-                deadline = time.perf_counter() + 900
-                while (not closed or outstanding) and time.perf_counter() < deadline:
-                    while True:
-                        try:
-                            t = tickets.get_nowait()
-                        except queue.Empty:
-                            break
-                        if t is None:
-                            closed = True
-                        else:
-                            outstanding.append(t)
-                    still = []
-                    for t in outstanding:
-                        rc, res = srv.poll(t, timeout_us=0, copy_primes=False)
-                        if rc == gb.SIEVE_ETIMEOUT:
-                            still.append(t)
-                            continue
-                        if res["status"] != gb.SIEVE_OK:
-                            errors.append(res)
-                        else:
-                            lat.append(res["latency_us"])
-                        srv.release(t)
-                    if len(still) == len(outstanding):
-                        time.sleep(0.0002)
-                    outstanding = still
-                if outstanding:
-                    errors.append(f"{len(outstanding)} requests unfinished after 900 s")
+                def collect():  # picks up finished results in any order and releases them (frees slots)
+                    outstanding, closed = [], False
+                    deadline = time.perf_counter() + 900
+                    while (not closed or outstanding) and time.perf_counter() < deadline:
+                        while True:
+                            try:
+                                t = tickets.get_nowait()
+                            except queue.Empty:
+                                break
+                            if t is None:
+                                closed = True
+                            else:
+                                outstanding.append(t)
+                        still = []
+                        for t in outstanding:
+                            rc, res = srv.poll(t, timeout_us=0, copy_primes=False)
+                            if rc == gb.SIEVE_ETIMEOUT:
+                                still.append(t)
+                                continue
+                            if res["status"] != gb.SIEVE_OK:
+                                errors.append(res)
+                            else:
+                                lat.append(res["latency_us"])
+                            srv.release(t)
+                        if len(still) == len(outstanding):
+                            time.sleep(0.0002)
+                        outstanding = still
+                    if outstanding:
+                        errors.append(f"{len(outstanding)} requests unfinished after 900 s")
 
-            th = threading.Thread(target=collect)
-            th.start()
-            t0 = time.perf_counter()
-            rejected = 0
-            for r in reqs:
-                now = time.perf_counter() - t0
-                if r.arrival_s > now:
-                    time.sleep(r.arrival_s - now)
-                kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
-                rc, t = srv.submit(r.lo, r.hi, kind)
-                give_up = time.perf_counter() + 120
-                while rc == gb.SIEVE_EBUSY:  # admission is full: retry (bounded)
-                    if time.perf_counter() > give_up:
-                        tickets.put(None)
-                        th.join()
-                        raise RuntimeError("served: a request was refused for 120 s")
-                    rejected += 1
-                    time.sleep(0.0005)
+                th = threading.Thread(target=collect)
+                th.start()
+                t0 = time.perf_counter()
+                rejected = 0
+                for r in reqs:
+                    now = time.perf_counter() - t0
+                    if r.arrival_s > now:
+                        time.sleep(r.arrival_s - now)
+                    kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
                     rc, t = srv.submit(r.lo, r.hi, kind)
-                tickets.put(t)
-            tickets.put(None)
-            th.join()
-            wall = time.perf_counter() - t0
-            if errors:
-                raise RuntimeError(f"served requests failed: {errors[:3]}")
-        ints = sum(r.hi - r.lo for r in reqs)
-        results.append({"offered_req_s": rate, "requests": len(reqs), "integers_per_s": ints / wall,
-                        "p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3,
-                        "wall_s": wall, "busy_retries": rejected})
-    best = max(r["integers_per_s"] for r in results)
-    line = {"metric": METRIC, "value": best, "unit": METRIC, "n_gpus": 1, "steps": len(rates), "warmup": 0,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "served: seeded Poisson stream, 80% count / 20% list, lo log-uniform "
-                                   "[0, 1e12], w log-uniform [1e4, 1e9]", "requests_per_rate": args.requests},
-            "rates": results,
-            "plain_single_range": {"value": 10**11 / (plain_ms * 1e-3), "unit": METRIC, "range": "[0, 1e11)"}}
+                    give_up = time.perf_counter() + 120
+                    while rc == gb.SIEVE_EBUSY:  # admission is full: retry (bounded)
+                        if time.perf_counter() > give_up:
+                            tickets.put(None)
+                            th.join()
+                            raise RuntimeError("served: a request was refused for 120 s")
+                        rejected += 1
+                        time.sleep(0.0005)
+                        rc, t = srv.submit(r.lo, r.hi, kind)
+                    tickets.put(t)
+                tickets.put(None)
+                th.join()
+                wall = time.perf_counter() - t0
+                if errors:
+                    raise RuntimeError(f"served requests failed: {errors[:3]}")
+            ints = sum(r.hi - r.lo for r in reqs)
+            results.append({"offered_req_s": rate, "requests": len(reqs), "integers_per_s": ints / wall,
+                            "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                            "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                            "wall_s": wall, "busy_retries": rejected})
+    best_i = max(range(len(results)), key=lambda i: results[i]["integers_per_s"])
+    best = results[best_i]
+    reqs = all_reqs[best_i]
+    units = sum(r.hi - r.lo for r in reqs)
+    med = sorted(r.lo for r in reqs)[len(reqs) // 2]
+    plain = _plain_same_integers(sv, med, units)
+    peaks, peak_kind = _peaks()
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    clears = sum(sv.crossing_work(r.lo, r.hi) for r in reqs)
+    atomics = sum(sv.crossing_work(r.lo, r.hi, 61) for r in reqs)
+    probe = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_CONFLICT_FREE)
     sv.close()
+    out = {"value": best["integers_per_s"], "unit": METRIC,
+           "config": {"workload": "served: seeded Poisson stream, 80% count / 20% list, lo log-uniform "
+                                  "[0, 1e12], w log-uniform [1e4, 1e9]", "seed": 1205,
+                      "value_from": f"offered {best['offered_req_s']:.0f} req/s (the best of the rates)",
+                      "timing": "host wall clock from the first arrival to the last result"},
+           "rates": results,
+           "vs_plain": best["integers_per_s"] / plain["value"],
+           "plain_single_range": plain,
+           "roofline": _op_roofline(clears, best["wall_s"], n_sms, peaks, peak_kind, probe, atomics),
+           "clocks": clk.summary()}
+    if cpu:
+        out["cpu_baseline"] = _cpu_intervals([(r.lo, r.hi, r.kind) for r in reqs])
+    return out
+
+
+def run_served(args):
+    rates = [float(r) for r in args.rates.split(",")]
+    out = served_measure(rates, args.requests)
+    line = {"metric": METRIC, "value": out["value"], "unit": METRIC, "n_gpus": 1, "steps": len(rates),
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": out["config"]}
+    line.update({k: v for k, v in out.items() if k not in line})
     print(json.dumps(line))
+    return 0
+
+
+def run_peaks(args):
+    import torch
+    import paper_1205_4883_gb300 as gb
+    torch.cuda.set_device(0)
+    with gb.Sieve(1 << 20) as sv:
+        with ClockSampler(_gpu_id(0)) as clk:
+            rates = _probe_rates(sv)
+    print(json.dumps({"metric": "roofline probes", "probes": rates, "clocks": clk.summary()}))
     return 0
 
 
@@ -536,10 +758,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lo", type=int, default=0, help="with --hi: sieve [lo, hi) of each rank's block instead")
     ap.add_argument("--hi", type=int, default=None)
-    ap.add_argument("--workload", default="pi1e12", choices=["pi1e12", "batched", "served", "range2p32", "pi1e7"],
+    ap.add_argument("--workload", default="pi1e12",
+                    choices=["pi1e12", "batched", "served", "range2p32", "pi1e7", "peaks"],
                     help="pi1e12 (default, the headline line), batched, served, range2p32 (bitmap and "
-                         "u32 list of [0, 2^32)) or pi1e7 (count, bitmap and list of [0, 10^7))")
+                         "u32 list of [0, 2^32)), pi1e7 (count, bitmap and list of [0, 10^7)) or peaks")
     ap.add_argument("--rates", default="100,300,1000,3000,10000,30000", help="served: offered loads, req/s")
+    ap.add_argument("--default-rates", default="1000,10000,30000",
+                    help="served rates of the sub-object in the default line")
+    ap.add_argument("--no-sub", action="store_true", help="default line without the batched/served sub-objects")
     ap.add_argument("--requests", type=int, default=0,
                     help="served: requests per rate (0: 1 s of arrivals, between 300 and 10000)")
     args = ap.parse_args()
@@ -555,9 +781,20 @@ def main():
         return run_outputs(args, 0, 1 << 32, "[0, 2^32): odd-only bitmap and u32 prime list", False)
     if args.workload == "pi1e7":
         return run_outputs(args, 0, 10**7, "[0, 10^7): count, odd-only bitmap and u32 prime list", True)
+    if args.workload == "peaks":
+        return run_peaks(args)
     line = run_gpu(args)
     ws, rank, _ = _dist()
     if rank == 0 and line is not None:
+        if ws == 1 and not args.no_sub:
+            # the metric's "batched/served vs plain": both on the same GPU, same process
+            line["batched"] = batched_measure(args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+            line["served"] = served_measure([float(r) for r in args.default_rates.split(",")],
+                                            cpu=not args.no_cpu_baseline)
+            line["pi1e7"] = outputs_measure(0, 10**7, "[0, 10^7): count, odd-only bitmap and u32 prime list",
+                                            True, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+            line["range2p32"] = outputs_measure(0, 1 << 32, "[0, 2^32): odd-only bitmap and u32 prime list",
+                                                False, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample()
         print(json.dumps(line))

@@ -407,3 +407,16 @@ def test_miller_rabin_path_rejects_strong_pseudoprimes():
             got = [int(v) for v in s.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)]
             assert n not in got
             assert got == [x for x in range(lo, hi) if mr_is_prime(x)]
+
+
+def test_roofline_probes_report_plausible_rates(sv):
+    # measured denominators: lane-ops per SM clock (at most 32, one per lane) and GB/s
+    cf = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_CONFLICT_FREE)
+    rnd = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_RANDOM)
+    st = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_STORE_CONFLICT_FREE)
+    assert 4 < rnd < cf <= 32.5 and 4 < st <= 32.5
+    buf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    gbs = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_HBM_WRITE, buf)
+    assert 1000 < gbs < 20000
+    with pytest.raises(gb.SieveError):
+        gb.sieve_probe(sv.ctx, 99)
