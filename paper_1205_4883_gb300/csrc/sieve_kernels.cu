@@ -605,8 +605,12 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             // been seen in normal runs.
             if (s_tile_fail) break;
             // 1'. the further patterns (primes 23..59), ANDed in 16 bytes at a time
-            //     from their L2-resident shifted copies
-            if (P.xtile0) {
+            //     from their L2-resident shifted copies.  In count mode the AND is
+            //     fused into the popcount epilogue instead (step 4), which reads every
+            //     word anyway -- except in the segment holding wheel bytes 0 and 1,
+            //     whose fix-up (step 3) must come after the patterns.
+            const bool fuse_x = MODE == kModeCount && P.xtile0 && !(B0 <= 1 && B0 + (int64_t)L > 0);
+            if (P.xtile0 && !fuse_x) {
                 const uint4 *x0 = reinterpret_cast<const uint4 *>(P.xtile0 + (s_xph[0] & 15u) * kXTileStride0 +
                                                                   (s_xph[0] & ~15u));
                 const uint4 *x1 = reinterpret_cast<const uint4 *>(P.xtile1 + (s_xph[1] & 15u) * kXTileStride1 +
@@ -777,15 +781,37 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                 // 4. popcount of the bits in [lo, hi); a range on the Miller-Rabin
                 //    path also leaves its raw wheel words for k_mr_filter
                 uint32_t *const raw = rd.mr ? rd.bitmap : nullptr;
+                const uint4 *x0 = nullptr, *x1 = nullptr, *x2 = nullptr;
+                if (fuse_x) {  // the further patterns' words for this segment (step 1')
+                    x0 = reinterpret_cast<const uint4 *>(P.xtile0 + (s_xph[0] & 15u) * kXTileStride0 +
+                                                         (s_xph[0] & ~15u));
+                    x1 = reinterpret_cast<const uint4 *>(P.xtile1 + (s_xph[1] & 15u) * kXTileStride1 +
+                                                         (s_xph[1] & ~15u));
+                    x2 = reinterpret_cast<const uint4 *>(P.xtile2 + (s_xph[2] & 15u) * kXTileStride2 +
+                                                         (s_xph[2] & ~15u));
+                }
                 if (!raw && lo_rel <= 0 && hi_rel >= 30 * (int64_t)L) {
                     // the whole segment lies in [lo, hi): no masks, 16-byte loads
-                    for (uint32_t q = tid; q < L / 16; q += blockDim.x) {
-                        const uint4 v = smem4[q];
-                        cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+                    if (fuse_x) {
+                        for (uint32_t q = tid; q < L / 16; q += blockDim.x) {
+                            const uint4 a = __ldg(x0 + q), b = __ldg(x1 + q), c = __ldg(x2 + q);
+                            const uint4 v = smem4[q];
+                            cnt += __popc(v.x & a.x & b.x & c.x) + __popc(v.y & a.y & b.y & c.y) +
+                                   __popc(v.z & a.z & b.z & c.z) + __popc(v.w & a.w & b.w & c.w);
+                        }
+                    } else {
+                        for (uint32_t q = tid; q < L / 16; q += blockDim.x) {
+                            const uint4 v = smem4[q];
+                            cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+                        }
                     }
                 } else {
+                    const uint32_t *y0 = reinterpret_cast<const uint32_t *>(x0),
+                                   *y1 = reinterpret_cast<const uint32_t *>(x1),
+                                   *y2 = reinterpret_cast<const uint32_t *>(x2);
                     for (uint32_t w = tid; w < L / 4; w += blockDim.x) {
                         uint32_t v = seg32[w];
+                        if (fuse_x) v &= __ldg(y0 + w) & __ldg(y1 + w) & __ldg(y2 + w);
                         if (raw) raw[w] = v;
                         const int64_t wb = 120 * (int64_t)w;
                         if (wb < lo_rel || wb + 120 > hi_rel) v &= range_mask(wb, lo_rel, hi_rel);
