@@ -132,6 +132,36 @@ int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi,
                       size_t m, uint64_t *counts, uint32_t *const *bitmaps_dev);
 
 /*
+ * Launch parameters of one range of a batch (sieve_batch_count_params), so
+ * that ranges of different size classes are each sieved with their own
+ * choice inside the same launch -- the GPU form of the paper's Algorithm 1,
+ * which picks the work split of a block by its size.  A field left 0 takes the
+ * context's value (sieve_set_param).  Results never depend on these.
+ */
+typedef struct {
+    uint32_t seg_bytes;     /* segment bytes: a multiple of 32 in 1024 .. 229376 */
+    uint32_t wheel;         /* 30 or 210 (the mod-210 wheel serves count-only batches) */
+    uint64_t bucket_limit;  /* mod 30: base primes >= this go through bucket lists;
+                               1 << 62 for none */
+    uint32_t mid_limit;     /* base primes below this use the per-phase (mod 30) or
+                               per-class (mod 210) tier, larger ones the wheel walk */
+    uint32_t mr_percent;    /* as SIEVE_PARAM_MR_PERCENT; UINT32_MAX: never */
+} sieve_range_params;
+
+/*
+ * As sieve_batch_count, with params[i] (a host array of m, or NULL for the
+ * context's parameters everywhere) the launch parameters of range i.  The
+ * ranges on the mod-30 wheel are sieved by one persistent kernel launch and
+ * those on the mod-210 wheel by a second one; both are captured together in one
+ * CUDA graph (per batch shape) and replayed as one graph launch.  Ranges whose
+ * parameters call for bucket lists make the batch launch directly instead.
+ * SIEVE_EINVAL for an out-of-range field, or wheel 210 with bitmaps_dev set.
+ */
+int sieve_batch_count_params(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi,
+                             size_t m, const sieve_range_params *params, uint64_t *counts,
+                             uint32_t *const *bitmaps_dev);
+
+/*
  * Compaction that allocates no device memory, for callers that cannot call
  * cudaMalloc (code running inside a fixed memory arena, a real-time loop that
  * must not take the allocator's locks, or a plug-in whose host owns all

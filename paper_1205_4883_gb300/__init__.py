@@ -81,8 +81,14 @@ class sieve_server_counters(ctypes.Structure):
                 ("device_bytes_reserved", _u64)]
 
 
+class sieve_range_params(ctypes.Structure):
+    _fields_ = [("seg_bytes", ctypes.c_uint32), ("wheel", ctypes.c_uint32), ("bucket_limit", _u64),
+                ("mid_limit", ctypes.c_uint32), ("mr_percent", ctypes.c_uint32)]
+
+
 SIEVE_REQ_COUNT = 0
 SIEVE_REQ_LIST = 1
+MR_NEVER = 0xFFFFFFFF
 
 # name -> (restype, argtypes)
 _SIGS = {
@@ -96,6 +102,8 @@ _SIGS = {
     "sieve_list64": (_int, [_vp, _u64, _u64, _vp, _sz, _pu64]),
     "sieve_compact": (_int, [_vp, _vp, _u64, _u64, _vp, _sz, _pu64]),
     "sieve_batch_count": (_int, [_vp, _pu64, _pu64, _sz, _pu64, ctypes.POINTER(_vp)]),
+    "sieve_batch_count_params": (_int, [_vp, _pu64, _pu64, _sz, ctypes.POINTER(sieve_range_params), _pu64,
+                                        ctypes.POINTER(_vp)]),
     "sieve_set_param": (_int, [_vp, _int, _i64]),
     "sieve_get_param": (_int, [_vp, _int, ctypes.POINTER(_i64)]),
     "sieve_get_info": (_int, [_vp, ctypes.POINTER(sieve_info)]),
@@ -281,6 +289,53 @@ def sieve_batch_count(ctx: int, lo: Sequence[int], hi: Sequence[int], bitmaps=No
         bm = (_vp * max(m, 1))(*[(_ptr(b) or None) for b in bitmaps])
     as_u64 = lambda a: a.ctypes.data_as(_pu64)  # noqa: E731
     _check(ctx, load_library().sieve_batch_count(ctx, as_u64(lo_a), as_u64(hi_a), m, as_u64(cnt), bm))
+    return cnt[:m].tolist()
+
+
+_RANGE_FIELDS = ("seg_bytes", "wheel", "bucket_limit", "mid_limit", "mr_percent")
+
+
+def range_params_dtype():
+    """numpy dtype with the layout of sieve_range_params."""
+    import numpy as np
+    dt = np.dtype([("seg_bytes", "<u4"), ("wheel", "<u4"), ("bucket_limit", "<u8"),
+                   ("mid_limit", "<u4"), ("mr_percent", "<u4")])
+    assert dt.itemsize == ctypes.sizeof(sieve_range_params)
+    return dt
+
+
+def range_params_array(params):
+    """A sieve_range_params array from a sequence of dicts (missing fields: 0)."""
+    import numpy as np
+    pa = np.zeros(max(len(params), 1), dtype=range_params_dtype())
+    for f in _RANGE_FIELDS:
+        pa[f][:len(params)] = [int(p.get(f, 0) or 0) for p in params]
+    return pa
+
+
+def sieve_batch_count_params(ctx: int, lo: Sequence[int], hi: Sequence[int], params, bitmaps=None):
+    """Counts of m ranges with per-range launch parameters, one graph launch.
+    params: a sieve_range_params array (range_params_array) or a sequence of m
+    dicts with any of seg_bytes, wheel, bucket_limit, mid_limit, mr_percent
+    (missing or 0: the context's value)."""
+    import numpy as np
+    m = len(lo)
+    if len(hi) != m or len(params) < m:
+        raise ValueError("lo, hi and params differ in length")
+    lo_a = np.ascontiguousarray(lo, dtype=np.uint64) if m else np.zeros(1, np.uint64)
+    hi_a = np.ascontiguousarray(hi, dtype=np.uint64) if m else np.zeros(1, np.uint64)
+    cnt = np.zeros(max(m, 1), dtype=np.uint64)
+    if isinstance(params, np.ndarray) and params.dtype == range_params_dtype():
+        pa = np.ascontiguousarray(params)
+    else:
+        pa = range_params_array(params)
+    bm = None
+    if bitmaps is not None:
+        bm = (_vp * max(m, 1))(*[(_ptr(b) or None) for b in bitmaps])
+    as_u64 = lambda a: a.ctypes.data_as(_pu64)  # noqa: E731
+    _check(ctx, load_library().sieve_batch_count_params(
+        ctx, as_u64(lo_a), as_u64(hi_a), m, pa.ctypes.data_as(ctypes.POINTER(sieve_range_params)),
+        as_u64(cnt), bm))
     return cnt[:m].tolist()
 
 
@@ -489,26 +544,15 @@ class Sieve:
             if k in self._PARAM_IDS:
                 sieve_set_param(self.ctx, self._PARAM_IDS[k], int(v))
 
-    def batch_count_tuned(self, lo, hi, table=None):
-        """Counts of many ranges, grouped by autotuner size class; one launch per
-        class with that class's parameters."""
+    def batch_count_params(self, lo, hi, params, bitmaps=None):
+        return sieve_batch_count_params(self.ctx, lo, hi, params, bitmaps)
+
+    def batch_count_tuned(self, lo, hi, table=None, bitmaps=None):
+        """Counts of many ranges, each sieved with the launch parameters the
+        autotuner chose for its size class, all in one graph launch."""
         from . import autotune
         table = table if table is not None else autotune.load_table()
-        groups = {}
-        for i, (a, b) in enumerate(zip(lo, hi)):
-            groups.setdefault(autotune.class_key(a, b), []).append(i)
-        out = [0] * len(lo)
-        saved = {k: sieve_get_param(self.ctx, pid) for k, pid in self._PARAM_IDS.items()}
-        try:
-            for key, idx in groups.items():
-                self.apply_plan(saved)
-                self.apply_plan(table.get("classes", {}).get(key, {}))
-                counts = sieve_batch_count(self.ctx, [lo[i] for i in idx], [hi[i] for i in idx])
-                for i, c in zip(idx, counts):
-                    out[i] = c
-        finally:
-            self.apply_plan(saved)
-        return out
+        return sieve_batch_count_params(self.ctx, lo, hi, autotune.range_params_array(table, lo, hi), bitmaps)
 
     def set_param(self, param, value):
         sieve_set_param(self.ctx, param, value)

@@ -1,21 +1,28 @@
-"""Autotuner: pick launch parameters per size class of the sieved ranges.
+"""Autotuner: launch parameters per size class of the sieved ranges.
 
-A size class is (range start band, width band).  For each class a seeded set
-of representative intervals is sieved with every candidate parameter set
-(segment bytes, small-prime limit, threads per CTA, bucket limit, chunk size)
-and the fastest is kept.  The table is JSON:
+The paper's Algorithm 1 picks how a block is sieved from its size (one core
+for a short last block, two from both ends otherwise).  The GPU form is a
+table from a range's size class -- the band of its start and the band of its
+width -- to launch parameters: segment bytes, wheel (mod 30 or mod 210),
+bucket limit, the per-phase tier's limit and the Miller-Rabin threshold.
+``sieve_batch_count_params`` applies them per range inside one batched
+launch, so a batch mixing all classes is still one graph launch.
 
-    {"device": "...", "classes": {"<lo band>/<w band>": {"segment_bytes": ..., ...}}}
+For each class a seeded set of representative intervals is timed under a
+coordinate search: starting from the context's defaults, each parameter in
+turn takes the value of its candidates that is fastest with the others held,
+for two passes.  The defaults are a candidate throughout, so a class's
+choice is never slower than the defaults on its own sample.  The table is
+JSON:
 
-``plan_for(table, lo, hi)`` returns the parameters for one range, and
-``Sieve.apply_plan`` / ``batch_count_tuned`` in the package use them.
+    {"device": "...", "classes": {"<lo band>/<w band>": {"seg_bytes": ..., ...}},
+     "timing_ms": {...}}
 
   python -m paper_1205_4883_gb300.autotune [--out tuned.json] [--quick]
 """
 from __future__ import annotations
 
 import argparse
-import itertools
 import json
 import math
 import os
@@ -28,11 +35,22 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_TABLE = os.path.join(HERE, "tuned.json")
 
 # band edges (log10): start of the range and its width
-LO_BANDS = [(0, 10), (10, 13), (13, 19)]
-W_BANDS = [(0, 5), (5, 7), (7, 9), (9, 19)]
+LO_BANDS = [(0, 8), (8, 10), (10, 12), (12, 13), (13, 19)]
+W_BANDS = [(0, 4), (4, 5), (5, 6), (6, 7), (7, 19)]
 
-PARAM_KEYS = {"segment_bytes": 1, "threads": 2, "small_limit": 3, "ctas_per_sm": 4,
-              "chunk_segments": 5, "bucket_limit": 6, "cursor_mb": 7, "mid_limit": 9}
+MR_NEVER = 0xFFFFFFFF
+BUCKETS_OFF = 1 << 62
+# candidates per parameter (0 = the context's default for that field)
+CANDIDATES = {
+    "seg_bytes": [0, 32768, 65536, 131072],
+    "wheel": [0, 210],
+    "bucket_limit": [0, 229376, 1 << 20],
+    "mid_limit": [0, 4096, 16384],
+    "mr_percent": [0, 5, 25, 100],
+}
+FIELDS = tuple(CANDIDATES)
+# a candidate replaces the current choice only if it is this much faster
+MIN_GAIN = 0.03
 
 
 def band(x: int, bands) -> int:
@@ -49,6 +67,37 @@ def class_key(lo: int, hi: int) -> str:
 
 def plan_for(table: dict, lo: int, hi: int) -> Dict[str, int]:
     return dict(table.get("classes", {}).get(class_key(lo, hi), {}))
+
+
+def range_params(table: dict, lo: Sequence[int], hi: Sequence[int]) -> List[Dict[str, int]]:
+    """The per-range launch parameters (sieve_range_params fields) for a batch."""
+    classes = table.get("classes", {})
+    return [{k: v for k, v in classes.get(class_key(a, b), {}).items() if k in FIELDS} for a, b in zip(lo, hi)]
+
+
+def range_params_array(table: dict, lo: Sequence[int], hi: Sequence[int]):
+    """range_params as a sieve_range_params array, built with numpy (one table row
+    per size class, gathered by each range's class index)."""
+    import numpy as np
+
+    from . import range_params_array as to_array
+    lo_a = np.asarray(lo, dtype=np.float64)
+    w_a = np.asarray(hi, dtype=np.float64) - lo_a
+
+    def bands_of(x, bands):
+        lx = np.log10(np.maximum(x, 1.0))
+        idx = np.full(len(x), len(bands) - 1, dtype=np.int64)
+        for i in range(len(bands) - 1, -1, -1):
+            a, b = bands[i]
+            idx[(lx >= a) & (lx < b)] = i
+        return idx
+
+    li, wi = bands_of(lo_a, LO_BANDS), bands_of(w_a, W_BANDS)
+    rows = [{k: v for k, v in table.get("classes", {}).get(f"{a}/{b}", {}).items() if k in FIELDS}
+            for a in range(len(LO_BANDS)) for b in range(len(W_BANDS))]
+    per_class = to_array(rows)
+    out = per_class[li * len(W_BANDS) + wi] if len(lo) else per_class[:0]
+    return np.ascontiguousarray(out)
 
 
 def load_table(path: str = DEFAULT_TABLE) -> dict:
@@ -71,54 +120,66 @@ def sample_class(lo_band, w_band, n: int, seed: int, hi_max: int) -> Tuple[List[
     return los, his
 
 
-def candidates(quick: bool):
-    segs = [65536, 229376] if quick else [32768, 65536, 131072, 229376]
-    smalls = [448] if quick else [256, 448, 896]
-    threads = [1024] if quick else [512, 1024]
-    buckets = [1 << 62, 0]
-    chunks = [16]
-    for seg, small, thr, bl, ch in itertools.product(segs, smalls, threads, buckets, chunks):
-        yield {"segment_bytes": seg, "small_limit": small, "threads": thr, "bucket_limit": bl,
-               "chunk_segments": ch, "ctas_per_sm": 1}
+def _time_batch(sv, los, his, params, reps: int) -> float:
+    """Median host time (ms) of one batched call with `params` for every range; the
+    parameter array is built once, outside the timed calls."""
+    import torch
+
+    from . import range_params_array as to_array
+    pa = to_array([params] * len(los))
+    sv.batch_count_params(los, his, pa)  # warm-up (and graph capture)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        sv.batch_count_params(los, his, pa)
+        ts.append(time.perf_counter() - t0)
+    return sorted(ts)[len(ts) // 2] * 1e3
 
 
-def tune(out: str = DEFAULT_TABLE, quick: bool = False, budget_s: float = 240.0) -> dict:
+def tune(out: str = DEFAULT_TABLE, quick: bool = False, budget_s: float = 300.0, hi_cap: int = 10**14 + 10**9 + 1,
+         passes: int = 2) -> dict:
     import torch
 
     from . import Sieve
     t_start = time.time()
-    hi_cap = 10**14 + 10**9 + 1
     sv = Sieve(hi_cap)
-    table = {"device": torch.cuda.get_device_name(0), "classes": {}, "timing_ms": {}}
-    cands = list(candidates(quick))
-    for (li, lb), (wi, wb) in itertools.product(enumerate(LO_BANDS), enumerate(W_BANDS)):
-        lb_c = (lb[0], min(lb[1], 14))
-        wb_c = (wb[0], min(wb[1], 9 if li < 2 else 8))
-        if lb_c[0] >= lb_c[1] or wb_c[0] >= wb_c[1]:
-            continue
-        n = 64 if wb_c[1] <= 7 else 8
-        los, his = sample_class(lb_c, wb_c, n, seed=1205 + 17 * li + wi, hi_max=hi_cap)
-        best, best_ms, timings = None, float("inf"), {}
-        for c in cands:
-            if time.time() - t_start > budget_s:
-                break
-            for k, v in c.items():
-                sv.set_param(PARAM_KEYS[k], v)
-            sv.batch_count(los, his)  # warm-up (and graph capture)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(3):
-                sv.batch_count(los, his)
-            ms = (time.perf_counter() - t0) / 3 * 1e3
-            timings[json.dumps(c, sort_keys=True)] = ms
-            if ms < best_ms:
-                best, best_ms = c, ms
-        if best is not None:
+    table = {"device": torch.cuda.get_device_name(0), "classes": {}, "timing_ms": {},
+             "method": f"coordinate search, {passes} passes, median of {3 if quick else 7} timed calls, "
+                       f"a change kept only if {MIN_GAIN:.0%} faster"}
+    reps = 3 if quick else 7
+    for li, lb in enumerate(LO_BANDS):
+        for wi, wb in enumerate(W_BANDS):
+            lb_c = (lb[0], min(lb[1], 14))
+            wb_c = (wb[0], min(wb[1], 8))
+            if lb_c[0] >= lb_c[1] or wb_c[0] >= wb_c[1]:
+                continue
+            n = 768 if wb_c[1] <= 6 else 96
+            los, his = sample_class(lb_c, wb_c, n, seed=1205 + 17 * li + wi, hi_max=hi_cap)
+            cur = {f: 0 for f in FIELDS}
+            base_ms = _time_batch(sv, los, his, cur, reps)
+            best_ms = base_ms
+            tried = 1
+            for _ in range(passes):
+                for f in FIELDS:
+                    if time.time() - t_start > budget_s:
+                        break
+                    if cur["wheel"] == 210 and f in ("bucket_limit", "mr_percent"):
+                        continue
+                    for v in CANDIDATES[f]:
+                        if v == cur[f]:
+                            continue
+                        trial = dict(cur, **{f: v})
+                        ms = _time_batch(sv, los, his, trial, reps)
+                        tried += 1
+                        if ms < best_ms * (1 - MIN_GAIN):  # a clear win, not timing noise
+                            best_ms, cur = ms, trial
             key = f"{li}/{wi}"
-            table["classes"][key] = best
-            table["timing_ms"][key] = {"best": best_ms, "integers": sum(h - l for l, h in zip(los, his)),
-                                       "candidates": len(timings)}
+            table["classes"][key] = {f: v for f, v in cur.items() if v}
+            table["timing_ms"][key] = {"defaults": base_ms, "best": best_ms, "intervals": n,
+                                       "integers": sum(h - l for l, h in zip(los, his)), "candidates": tried}
     sv.close()
+    table["budget_s_used"] = time.time() - t_start
     with open(out, "w") as f:
         json.dump(table, f, indent=1, sort_keys=True)
     return table
@@ -128,7 +189,8 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_TABLE)
     ap.add_argument("--quick", action="store_true")
-    ap.add_argument("--budget-s", type=float, default=240.0)
+    ap.add_argument("--budget-s", type=float, default=300.0)
     a = ap.parse_args()
     t = tune(a.out, a.quick, a.budget_s)
     print(json.dumps(t["classes"], indent=1))
+    print(json.dumps(t["timing_ms"], indent=1))

@@ -75,10 +75,28 @@ struct CursorStore {
     size_t entries = 0;
 };
 
+// A captured batch: m ranges on the mod-30 wheel in `mode` (count or bitmap)
+// with `smem` bytes of shared memory per CTA, and m210 count-only ranges on the
+// mod-210 wheel with smem210 bytes.
 struct GraphKey {
-    size_t m;
+    size_t m, m210;
     int mode;
-    bool operator<(const GraphKey &o) const { return m != o.m ? m < o.m : mode < o.mode; }
+    uint32_t smem, smem210;
+    bool operator<(const GraphKey &o) const {
+        if (m != o.m) return m < o.m;
+        if (m210 != o.m210) return m210 < o.m210;
+        if (mode != o.mode) return mode < o.mode;
+        if (smem != o.smem) return smem < o.smem;
+        return smem210 < o.smem210;
+    }
+};
+
+// Per-range overrides of a launch's parameters (0: the launch's Params).  The
+// segment size of a range is its RangeDesc::seg_bytes, set when it is planned.
+struct RangeOverride {
+    uint32_t mid_limit = 0;      // primes below this use the per-phase (mod 30) / per-class (mod 210) tier
+    uint64_t bucket_limit = 0;   // primes >= this go through the bucket lists (mod 30)
+    uint32_t mr_percent = 0;     // Miller-Rabin threshold; UINT32_MAX: never
 };
 
 }  // namespace gbs
@@ -106,6 +124,7 @@ struct sieve_ctx {
 
     gbs::Params params;
     gbs::LaunchBuffers lb;
+    gbs::LaunchBuffers lb210;  // the mod-210 ranges of a batch whose ranges use both wheels
     gbs::CompactScratch cs;
     gbs::BucketStore buckets;
     gbs::CursorStore cursors;
@@ -143,10 +162,11 @@ void free_compact_scratch(sieve_ctx *ctx, CompactScratch &cs);
 // accumulators and launches.  Bucket lists are used only if `bs` is given.
 RangeDesc plan_range210(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t seg_words);
 uint32_t w210_segment_words(const Params &prm);
+// ro (optional) holds per-range overrides of prm, one per range of lb.
 int launch_ranges210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, LaunchBuffers &lb, size_t m,
-                     CursorStore *cs);
+                     CursorStore *cs, const RangeOverride *ro = nullptr);
 int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
-                  BucketStore *bs, CursorStore *cs = nullptr);
+                  BucketStore *bs, CursorStore *cs = nullptr, const RangeOverride *ro = nullptr);
 
 // Compact the odd-only bitmap of [lo, hi) into out_dev (uint32 or uint64).
 // *n = primes in the range (2 included); SIEVE_ETRUNC if cap < *n.

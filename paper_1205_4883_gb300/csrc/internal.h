@@ -59,8 +59,13 @@ struct RangeDesc {
     uint64_t corr;          // primes the wheel cannot hold (2, 3, 5) in range
     uint32_t n_use;         // base primes with p * p < hi (prefix length)
     uint32_t mr;            // 1: sieve with the primes below 2^16, then Miller-Rabin (one segment)
+    // this range's launch parameters (ranges of one launch may differ):
+    uint32_t seg_bytes;     // segment size S (bytes; <= the launch's SieveLaunch::seg_bytes)
+    uint32_t mid_end;       // primes [small_end, mid_end) per-phase tier, [mid_end, ...) wheel walk
+    uint32_t bucket_first;  // primes [bucket_first, n_use) through the bucket lists (0xffffffff: none)
+    uint32_t reserved;
 };
-static_assert(sizeof(RangeDesc) == 72, "RangeDesc layout");
+static_assert(sizeof(RangeDesc) == 88, "RangeDesc layout");
 
 enum SieveMode : int { kModeCount = 0, kModeBitmap = 1 };
 
@@ -73,8 +78,8 @@ struct SieveLaunch {
     const uint32_t *primes;              // base primes, ascending, 2 first
     const uint64_t *magic;               // floor((2^64 - 1) / p) per prime
     uint32_t small_end;                  // primes [small_first, small_end) crossed warp-cooperatively
-    uint32_t mid_end;                    // primes [small_end, mid_end): per-phase sub-progressions
-    uint32_t bucket_first;               // primes [bucket_first, ...) go through the bucket lists
+    uint32_t mid_end;                    // the largest RangeDesc::mid_end of the launch (cost table end)
+    uint32_t bucket_first;               // the smallest RangeDesc::bucket_first of the launch
     uint32_t chunk_segs;                 // segments per work item, <= kMaxChunkSegments
     uint32_t *buckets;                   // grid x chunk_segs x bucket_cap entries
     uint32_t bucket_cap;                 // entries per segment list
@@ -87,7 +92,7 @@ struct SieveLaunch {
     uint32_t cursor_stride;              // large primes per CTA (from mid_end)
     const uint8_t *tile;                 // kTileCopies shifted copies of the pattern
     uint64_t tile_stride;                // bytes between copies
-    uint32_t seg_bytes;                  // S, multiple of 32, <= kMaxSegmentBytes
+    uint32_t seg_bytes;                  // the largest RangeDesc::seg_bytes (shared memory per CTA)
     uint32_t small_first;                // first prime of the small tier: kFirstCrossingPrime, or
                                          // kFirstCrossingPrimeX with the further patterns
     const uint8_t *xtile0, *xtile1, *xtile2;  // null, or copy 0 of each further pattern (mod-30 kernels)
@@ -154,10 +159,15 @@ cudaError_t launch_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *
                              uint64_t ntiles, int grid, cudaStream_t stream);
 cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint64_t ntiles,
                              unsigned long long *total, cudaStream_t stream);
+// With total != null, writes only if *total + base_index <= cap (else nothing).
 cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets,
                         uint64_t ntiles, uint64_t o0, uint32_t base_index, void *out,
-                        int out64, int grid, cudaStream_t stream);
+                        int out64, int grid, cudaStream_t stream,
+                        const unsigned long long *total = nullptr, uint64_t cap = 0);
 cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream);
+// out[0] = 2 if *total + 1 <= cap.
+cudaError_t launch_put_two_if_fits(void *out, int out64, const unsigned long long *total, uint64_t cap,
+                                   cudaStream_t stream);
 // *out = *count, or UINT64_MAX when *overflow is set.
 cudaError_t launch_finalize_count(const unsigned long long *count, const unsigned *overflow, uint64_t *out,
                                   cudaStream_t stream);

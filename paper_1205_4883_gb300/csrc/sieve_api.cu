@@ -208,9 +208,11 @@ RangeDesc plan_range(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t se
     if (diff < 0) diff += 960;
     const int64_t t0 = (int64_t)lo - diff;  // >= -930
     r.Bbase = t0 / 30;
+    r.bucket_first = 0xffffffffu;
     const uint64_t span = 30ull * seg_bytes;
     r.nseg = (uint64_t)(((int64_t)hi - t0 + (int64_t)span - 1) / (int64_t)span);
     r.n_use = primes_needed(ctx, hi);
+    r.seg_bytes = seg_bytes;
     uint64_t corr = (lo <= 2 && 2 < hi) ? 1 : 0;
     if (mode == kModeCount) corr += (lo <= 3 && 3 < hi ? 1 : 0) + (lo <= 5 && 5 < hi ? 1 : 0);
     r.corr = corr;
@@ -218,27 +220,41 @@ RangeDesc plan_range(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t se
 }
 
 int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &lb, size_t m, BucketStore *bs,
-                   CursorStore *cs, uint64_t *items_out) {
+                   CursorStore *cs, uint64_t *items_out, const RangeOverride *ro) {
     const std::vector<uint32_t> &h = ctx->h_primes;
     RangeDesc *rd = lb.h_ranges();
     uint64_t segs = 0;
-    uint32_t nmax = 0;
+    uint32_t nmax = 0, smax = 0;
     for (size_t i = 0; i < m; ++i) {
         segs += rd[i].nseg;
         if (rd[i].nseg) nmax = std::max(nmax, rd[i].n_use);
+        smax = std::max(smax, rd[i].seg_bytes);
     }
+    if (!smax) smax = prm.seg_bytes;
     const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
     const uint32_t small_end = first_at_least(h, prm.small_limit);
-    // per-phase sub-progressions for primes below S / 3 (about three hits per
-    // progression in a full segment): measured best on pi(10^12) among S / 8 .. S / 2.8
-    const uint32_t mid_lim = prm.mid_limit ? prm.mid_limit : std::max<uint32_t>(prm.seg_bytes / 3, 23);
-    const uint32_t mid_end = std::max(small_end, first_at_least(h, mid_lim));
-    const uint64_t blim = prm.bucket_limit ? prm.bucket_limit : prm.seg_bytes;
-    const uint32_t bfirst = std::max(first_at_least(h, blim), mid_end);
-    const bool buckets = bs && bfirst < nmax;
+    // Per range: per-phase sub-progressions for primes below S / 3 (about three hits
+    // per progression in a full segment; measured best on pi(10^12) among S / 8 ..
+    // S / 2.8), and bucket lists from the bucket limit on (never below the walk tier).
+    uint32_t mid_lo = 0xffffffffu, mid_hi = small_end, bfirst = 0xffffffffu;
+    for (size_t i = 0; i < m; ++i) {
+        const uint32_t ml = ro && ro[i].mid_limit ? ro[i].mid_limit : prm.mid_limit;
+        const uint32_t mid_lim = ml ? ml : std::max<uint32_t>(rd[i].seg_bytes / 3, 23);
+        rd[i].mid_end = std::max(small_end, first_at_least(h, mid_lim));
+        const uint64_t bl = ro && ro[i].bucket_limit ? ro[i].bucket_limit : prm.bucket_limit;
+        const uint32_t bf = std::max(first_at_least(h, bl ? bl : rd[i].seg_bytes), rd[i].mid_end);
+        rd[i].bucket_first = bs && rd[i].nseg && bf < rd[i].n_use ? bf : 0xffffffffu;
+        if (!rd[i].nseg) continue;
+        mid_lo = std::min(mid_lo, rd[i].mid_end);
+        mid_hi = std::max(mid_hi, rd[i].mid_end);
+        bfirst = std::min(bfirst, rd[i].bucket_first);
+    }
+    if (mid_lo == 0xffffffffu) mid_lo = mid_hi;
+    const bool buckets = bfirst != 0xffffffffu;
     // Per-CTA cursors for the large primes (4 B each) when they fit the budget
-    // and every offset fits 29 bits (p < 2^27); not with bucket lists.
-    const uint32_t n_large = nmax > mid_end ? nmax - mid_end : 0;
+    // and every offset fits 29 bits (p < 2^27); not with bucket lists.  A range's
+    // cursors are indexed from its own walk tier start, never below mid_lo.
+    const uint32_t n_large = nmax > mid_lo ? nmax - mid_lo : 0;
     bool cursors = cs && !buckets && n_large && h[nmax - 1] < (1u << 27) &&
                    (uint64_t)grid * n_large * 4 <= (uint64_t)prm.cursor_mb << 20;
     // Chunks (several segments per work item) pay off with bucket lists and
@@ -267,8 +283,10 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
     std::vector<size_t> scratch_at;
     for (size_t i = 0; i < m; ++i) {
         rd[i].mr = 0;
-        if (prm.mr_percent && rd[i].nseg == 1 && rd[i].n_use > mr_end && rd[i].hi > mr_square &&
-            (rd[i].hi - rd[i].lo) * 100 < (uint64_t)prm.mr_percent * (rd[i].n_use - mr_end)) {
+        const uint32_t mrp = !ro || !ro[i].mr_percent ? prm.mr_percent
+                             : ro[i].mr_percent == 0xffffffffu ? 0u : ro[i].mr_percent;
+        if (mrp && rd[i].nseg == 1 && rd[i].n_use > mr_end && rd[i].hi > mr_square &&
+            (rd[i].hi - rd[i].lo) * 100 < (uint64_t)mrp * (rd[i].n_use - mr_end)) {
             rd[i].mr = 1;
             lb.h_mr()[n_mr++] = (uint32_t)i;
             if (mode == kModeCount) {  // raw wheel words of the one segment
@@ -312,20 +330,21 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
     } else {
         L.small_first = kFirstCrossingPrime;
     }
-    L.seg_bytes = prm.seg_bytes;
+    L.seg_bytes = smax;
     L.chunk_segs = C;
     L.small_end = small_end;
-    L.mid_end = mid_end;
+    L.mid_end = mid_hi;
     L.mr_end = mr_end;
     L.mr_square = mr_square;
     L.mr_list = lb.d_mr();
     L.n_mr = n_mr;
-    L.bucket_first = 0xffffffffu;
+    L.bucket_first = bfirst;
     if (buckets) {
         // expected hits per full segment: 8 S / p per bucket prime (one per wheel
-        // class with probability S / p); the list capacity is that with a margin
+        // class with probability S / p); the list capacity is that with a margin,
+        // for the largest segment and the earliest bucket start of the launch
         double e = 0;
-        for (uint32_t i = bfirst; i < nmax; ++i) e += 8.0 * prm.seg_bytes / h[i];
+        for (uint32_t i = bfirst; i < nmax; ++i) e += 8.0 * smax / h[i];
         uint64_t cap = (uint64_t)(bs->slack * e) + 4096;
         cap = (cap + 31) & ~31ull;
         const size_t need = (size_t)grid * C * cap;
@@ -336,7 +355,6 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
             if (rc) return rc;
             bs->entries = need;
         }
-        L.bucket_first = bfirst;
         L.buckets = bs->d;
         L.bucket_cap = (uint32_t)cap;
     }
@@ -365,15 +383,16 @@ int enqueue_launch(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int m
         CK(cudaMemcpyAsync(lb.d_mr(), lb.h_mr(), n_list * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
     CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
     const SieveLaunch *d = reinterpret_cast<const SieveLaunch *>(lb.d_block);
-    if (grid > 0) CK(launch_sieve(mode, d, grid, prm.threads, prm.seg_bytes, stream));
+    const uint32_t smem = reinterpret_cast<const SieveLaunch *>(lb.h_block)->seg_bytes;  // the largest segment
+    if (grid > 0) CK(launch_sieve(mode, d, grid, prm.threads, smem, stream));
     if (mr_grid > 0) CK(launch_mr_filter(mode, d, mr_grid, stream));
     return SIEVE_OK;
 }
 
 int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
-                  BucketStore *bs, CursorStore *cs) {
+                  BucketStore *bs, CursorStore *cs, const RangeOverride *ro) {
     uint64_t items = 0;
-    int rc = prepare_launch(ctx, prm, mode, lb, m, bs, cs, &items);
+    int rc = prepare_launch(ctx, prm, mode, lb, m, bs, cs, &items, ro);
     if (rc) return rc;
     const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
     const uint32_t n_mr = reinterpret_cast<const SieveLaunch *>(lb.h_block)->n_mr;
@@ -399,6 +418,8 @@ RangeDesc plan_range210(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t
     const uint64_t span = 210ull * (seg_words / 3 * 2);
     r.nseg = (hi - 210ull * (uint64_t)r.Bbase + span - 1) / span;
     r.n_use = primes_needed(ctx, hi);
+    r.seg_bytes = 4 * seg_words;
+    r.bucket_first = 0xffffffffu;
     for (uint64_t q : {2, 3, 5, 7}) r.corr += lo <= q && q < hi;
     return r;
 }
@@ -407,22 +428,33 @@ RangeDesc plan_range210(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t
 // bucket lists, no Miller-Rabin path): fills the launch header; *items_out is
 // the number of work items.
 int prepare_launch210(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size_t m, CursorStore *cs,
-                      uint64_t *items_out) {
+                      uint64_t *items_out, const RangeOverride *ro) {
     const std::vector<uint32_t> &h = ctx->h_primes;
     RangeDesc *rd = lb.h_ranges();
     uint64_t segs = 0;
-    uint32_t nmax = 0;
+    uint32_t nmax = 0, smax = 0;
     for (size_t i = 0; i < m; ++i) {
         segs += rd[i].nseg;
         if (rd[i].nseg) nmax = std::max(nmax, rd[i].n_use);
+        smax = std::max(smax, rd[i].seg_bytes);
     }
-    const uint32_t sw = w210_segment_words(prm);
+    if (!smax) smax = 4 * w210_segment_words(prm);
     const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
     const uint32_t small_end = std::max(kFirstCrossingPrime, first_at_least(h, prm.small_limit210));
-    // primes below words / 6 have at least two hits per sub-progression in a full segment
-    const uint32_t mid_lim = prm.mid_limit210 ? prm.mid_limit210 : std::max<uint32_t>(sw / 6, 23);
-    const uint32_t mid_end = std::max(small_end, first_at_least(h, mid_lim));
-    const uint32_t n_large = nmax > mid_end ? nmax - mid_end : 0;
+    // per range: primes below words / 6 have at least two hits per sub-progression in
+    // a full segment
+    uint32_t mid_lo = 0xffffffffu, mid_hi = small_end;
+    for (size_t i = 0; i < m; ++i) {
+        const uint32_t ml = ro && ro[i].mid_limit ? ro[i].mid_limit : prm.mid_limit210;
+        const uint32_t mid_lim = ml ? ml : std::max<uint32_t>(rd[i].seg_bytes / 4 / 6, 23);
+        rd[i].mid_end = std::max(small_end, first_at_least(h, mid_lim));
+        rd[i].bucket_first = 0xffffffffu;
+        if (!rd[i].nseg) continue;
+        mid_lo = std::min(mid_lo, rd[i].mid_end);
+        mid_hi = std::max(mid_hi, rd[i].mid_end);
+    }
+    if (mid_lo == 0xffffffffu) mid_lo = mid_hi;
+    const uint32_t n_large = nmax > mid_lo ? nmax - mid_lo : 0;
     bool cursors = cs && n_large && h[nmax - 1] < (1u << 27) &&
                    (uint64_t)grid * n_large * 4 <= (uint64_t)prm.cursor_mb << 20;
     uint32_t C = prm.chunk_segs;
@@ -444,11 +476,11 @@ int prepare_launch210(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size
     L.overflow = reinterpret_cast<unsigned *>(lb.d_acc + m + 1);
     L.primes = ctx->d_primes;
     L.magic = ctx->d_magic;
-    L.seg_bytes = 4 * sw;
+    L.seg_bytes = smax;
     L.small_first = kFirstCrossingPrime;
     L.chunk_segs = C;
     L.small_end = small_end;
-    L.mid_end = mid_end;
+    L.mid_end = mid_hi;
     L.bucket_first = 0xffffffffu;
     if (cursors && C > 1) {
         const size_t need = (size_t)grid * n_large;
@@ -470,17 +502,17 @@ int prepare_launch210(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size
 int enqueue_launch210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, LaunchBuffers &lb, size_t m, int grid) {
     CK(cudaMemcpyAsync(lb.d_block, lb.h_block, kLaunchHeader + m * sizeof(RangeDesc), cudaMemcpyHostToDevice, stream));
     CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
+    const uint32_t smem = (reinterpret_cast<const SieveLaunch *>(lb.h_block)->seg_bytes + 15) & ~15u;
     if (grid > 0)
         CK(launch_sieve210(reinterpret_cast<const SieveLaunch *>(lb.d_block), ctx->d_tab210, ctx->d_tile210,
-                           ctx->tile210_stride, grid, prm.threads, (4 * w210_segment_words(prm) + 15) & ~15u,
-                           stream));
+                           ctx->tile210_stride, grid, prm.threads, smem, stream));
     return SIEVE_OK;
 }
 
 int launch_ranges210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, LaunchBuffers &lb, size_t m,
-                     CursorStore *cs) {
+                     CursorStore *cs, const RangeOverride *ro) {
     uint64_t items = 0;
-    int rc = prepare_launch210(ctx, prm, lb, m, cs, &items);
+    int rc = prepare_launch210(ctx, prm, lb, m, cs, &items, ro);
     if (rc) return rc;
     const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
     return enqueue_launch210(ctx, stream, prm, lb, m, (int)std::min<uint64_t>(grid, items));
@@ -497,18 +529,24 @@ int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const 
     uint64_t total = 0;
     const int grid = ctx->num_sms * 8;
     if (ntiles) {
+        // popcounts, scan, then the list itself, all enqueued at once: the emitting
+        // kernels read the total on the device and write only if the list fits in cap
         CK(launch_tile_popc(bitmap_dev, nwords, cs.counts, ntiles, grid, stream));
         CK(launch_tile_scan(cs.counts, cs.offsets, ntiles, cs.d_total, stream));
+        if (out_dev) {
+            if (two) CK(launch_put_two_if_fits(out_dev, out64, cs.d_total, cap, stream));
+            CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, lo | 1, two, out_dev, out64, grid, stream,
+                           cs.d_total, cap));
+        }
         CK(cudaMemcpyAsync(cs.h_total, cs.d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
         total = *cs.h_total;
     }
     *n = total + two;
-    if (*n > cap) return fail(ctx, SIEVE_ETRUNC, "output capacity below the prime count");
-    if (*n == 0) return SIEVE_OK;
-    if (!out_dev) return fail(ctx, SIEVE_EINVAL, "null output");
-    if (two) CK(launch_put_two(out_dev, out64, stream));
-    if (ntiles) CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, lo | 1, two, out_dev, out64, grid, stream));
+    if (*n > cap) return fail(ctx, SIEVE_ETRUNC, "output capacity below the prime count");  // nothing written
+    if (*n == 0 || ntiles) return SIEVE_OK;
+    // no odd integer in the range: the list is [2]
+    CK(launch_put_two(out_dev, out64, stream));
     CK(cudaStreamSynchronize(stream));
     return SIEVE_OK;
 }
@@ -685,40 +723,50 @@ int bitmap_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, uin
     return SIEVE_OK;
 }
 
-// A batched launch replayed from a CUDA graph captured once per (ranges, mode):
-// block copy, accumulator clear, the persistent sieve kernel over the full
-// grid (CTAs without work exit at once) and the copy-back of the counts.  The
-// launch parameters and range descriptors live in the pinned block that the
-// graph's first copy reads, so a replay only needs the block refreshed.
-// Batches that need bucket lists are launched directly (*used = false).
-constexpr int kModeCount210 = 2;  // graph key of count launches on the mod-210 wheel
-
-int batch_graph(sieve_ctx *ctx, int mode, size_t m, bool *used) {
+// A batched launch replayed from a CUDA graph captured once per GraphKey: for
+// the mod-30 ranges (ctx->lb, m of them) the block copy, accumulator clear and
+// persistent sieve kernel over the full grid (CTAs without work exit at once),
+// the same for the mod-210 ranges (ctx->lb210, m210 of them), and the copy-back
+// of both sets of counts.  The launch parameters and range descriptors live in
+// the pinned blocks that the graph's first copies read, so a replay only needs
+// the blocks refreshed.  Batches that need bucket lists are not captured
+// (*used = false).  ro / ro210: per-range overrides (or null).
+int batch_graph(sieve_ctx *ctx, int mode, size_t m, size_t m210, const RangeOverride *ro,
+                const RangeOverride *ro210, bool *used) {
     *used = false;
     const Params &prm = ctx->params;
     uint64_t items = 0;
-    int rc = mode == kModeCount210 ? prepare_launch210(ctx, prm, ctx->lb, m, &ctx->cursors, &items)
-                                   : prepare_launch(ctx, prm, mode, ctx->lb, m, nullptr, &ctx->cursors, &items);
-    if (rc) return rc;
-    if (mode != kModeCount210) {
-        const uint64_t blim = prm.bucket_limit ? prm.bucket_limit : prm.seg_bytes;
-        uint32_t nmax = 0;
-        for (size_t i = 0; i < m; ++i)
-            if (ctx->lb.h_ranges()[i].nseg) nmax = std::max(nmax, ctx->lb.h_ranges()[i].n_use);
-        if (first_at_least(ctx->h_primes, blim) < nmax) return SIEVE_OK;
+    int rc = SIEVE_OK;
+    if (m) {
+        rc = prepare_launch(ctx, prm, mode, ctx->lb, m, &ctx->buckets, &ctx->cursors, &items, ro);
+        if (rc) return rc;
+        if (reinterpret_cast<const SieveLaunch *>(ctx->lb.h_block)->bucket_first != 0xffffffffu) return SIEVE_OK;
+    }
+    // mod-210 cursors only when the mod-30 launch does not use the same store
+    CursorStore *cs210 = m && reinterpret_cast<const SieveLaunch *>(ctx->lb.h_block)->cursors ? nullptr
+                                                                                               : &ctx->cursors;
+    if (m210) {
+        rc = prepare_launch210(ctx, prm, ctx->lb210, m210, cs210, &items, ro210);
+        if (rc) return rc;
     }
     if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
-    const GraphKey key{m, mode};
+    const uint32_t smem = m ? reinterpret_cast<const SieveLaunch *>(ctx->lb.h_block)->seg_bytes : 0;
+    const uint32_t smem210 = m210 ? reinterpret_cast<const SieveLaunch *>(ctx->lb210.h_block)->seg_bytes : 0;
+    const GraphKey key{m, m210, mode, smem, smem210};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
         const int grid = ctx->num_sms * prm.ctas_per_sm;
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        rc = mode == kModeCount210 ? enqueue_launch210(ctx, ctx->capture_stream, prm, ctx->lb, m, grid)
-                                   : enqueue_launch(ctx, ctx->capture_stream, prm, mode, ctx->lb, m, grid,
-                                                    4 * ctx->num_sms, m);
-        cudaError_t e1 = cudaMemcpyAsync(ctx->lb.h_acc, ctx->lb.d_acc + 1, (m + 1) * sizeof(unsigned long long),
-                                         cudaMemcpyDeviceToHost, ctx->capture_stream);
+        if (m) rc = enqueue_launch(ctx, ctx->capture_stream, prm, mode, ctx->lb, m, grid, 4 * ctx->num_sms, m);
+        if (!rc && m210) rc = enqueue_launch210(ctx, ctx->capture_stream, prm, ctx->lb210, m210, grid);
+        cudaError_t e1 = cudaSuccess;
+        if (m)
+            e1 = cudaMemcpyAsync(ctx->lb.h_acc, ctx->lb.d_acc + 1, (m + 1) * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, ctx->capture_stream);
+        if (e1 == cudaSuccess && m210)
+            e1 = cudaMemcpyAsync(ctx->lb210.h_acc, ctx->lb210.d_acc + 1, (m210 + 1) * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, ctx->capture_stream);
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
         if (rc || e1 != cudaSuccess || e2 != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -732,7 +780,120 @@ int batch_graph(sieve_ctx *ctx, int mode, size_t m, bool *used) {
     }
     CK(cudaGraphLaunch(it->second, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if ((m && (ctx->lb.h_acc[m] & 2ull)) || (m210 && (ctx->lb210.h_acc[m210] & 2ull)) || ctx->params.fault_wait)
+        return fail(ctx, SIEVE_EDEVICE, "a device-side wait hit its limit");
     *used = true;
+    return SIEVE_OK;
+}
+
+int ensure_launch210(sieve_ctx *ctx, size_t m) {
+    if (m <= ctx->lb210.cap) return SIEVE_OK;
+    drop_graphs(ctx);  // they reference the old buffers
+    return alloc_launch_buffers(ctx, ctx->lb210, m);
+}
+
+// Count m ranges (and write their bitmaps if bitmaps_dev is set) with per-range
+// parameters rp (or the context's for all, rp = null): the ranges on each wheel
+// are sieved by one persistent launch, both captured in one CUDA graph.
+int batch_impl(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t m, const sieve_range_params *rp,
+               uint64_t *counts, uint32_t *const *bitmaps_dev) {
+    const Params &prm = ctx->params;
+    const int mode = bitmaps_dev ? kModeBitmap : kModeCount;
+    // resolve each range's wheel and segment size
+    std::vector<uint8_t> w210(m, 0);
+    std::vector<uint32_t> seg(m, prm.seg_bytes);
+    size_t n210 = 0;
+    for (size_t i = 0; i < m; ++i) {
+        const uint32_t wheel = rp && rp[i].wheel ? rp[i].wheel : (uint32_t)prm.wheel;
+        if (bitmaps_dev && wheel == 210 && rp && rp[i].wheel == 210)
+            return fail(ctx, SIEVE_EINVAL, "the mod-210 wheel has no bitmap output");
+        w210[i] = !bitmaps_dev && wheel == 210;
+        n210 += w210[i];
+        if (rp && rp[i].seg_bytes) seg[i] = rp[i].seg_bytes;
+    }
+    const size_t n30 = m - n210;
+    int rc = ensure_launch(ctx, std::max<size_t>(n30, 1));
+    if (rc) return rc;
+    if (n210) {
+        rc = ensure_launch210(ctx, n210);
+        if (rc) return rc;
+    }
+    auto plan = [&](size_t i) {
+        return w210[i] ? plan_range210(ctx, lo[i], hi[i], std::max<uint32_t>(std::min(seg[i], kW210MaxSegmentBytes) / 4 / 3 * 3, 3))
+                       : plan_range(ctx, lo[i], hi[i], seg[i], mode, bitmaps_dev ? bitmaps_dev[i] : nullptr);
+    };
+    // Launch order (SIEVE_PARAM_BATCH_ORDER): as given, heaviest first, or heaviest
+    // and lightest alternating -- GPU forms of sieving the last blocks from both
+    // ends, since persistent CTAs take work items in launch order.  Estimated work
+    // of a range: every segment visits its n_use base primes (about 3 warp
+    // instructions each) and crosses 0.16 warp instructions per integer.
+    std::vector<uint32_t> &order = ctx->batch_order;
+    order.resize(m);
+    for (size_t i = 0; i < m; ++i) order[i] = (uint32_t)i;
+    if (prm.batch_order) {
+        std::vector<double> cost(m);
+        for (size_t i = 0; i < m; ++i) {
+            const RangeDesc r = plan(i);
+            cost[i] = 3.0 * (double)r.nseg * r.n_use + 0.16 * (double)(hi[i] - lo[i]);
+        }
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+        if (prm.batch_order == 2) {  // heaviest, lightest, second heaviest, ...
+            std::vector<uint32_t> mixed;
+            mixed.reserve(m);
+            for (size_t a = 0, b = m; a < b;) {
+                mixed.push_back(order[a++]);
+                if (a < b) mixed.push_back(order[--b]);
+            }
+            order.swap(mixed);
+        }
+    }
+    // launch position of each range on its wheel
+    std::vector<uint32_t> pos30, pos210;
+    std::vector<RangeOverride> ro30, ro210;
+    pos30.reserve(n30);
+    pos210.reserve(n210);
+    for (size_t k = 0; k < m; ++k) {
+        const uint32_t i = order[k];
+        RangeOverride o;
+        if (rp) {
+            o.mid_limit = rp[i].mid_limit;
+            o.bucket_limit = rp[i].bucket_limit;
+            o.mr_percent = rp[i].mr_percent;
+        }
+        if (w210[i]) {
+            ctx->lb210.h_ranges()[pos210.size()] = plan(i);
+            pos210.push_back(i);
+            ro210.push_back(o);
+        } else {
+            ctx->lb.h_ranges()[pos30.size()] = plan(i);
+            pos30.push_back(i);
+            ro30.push_back(o);
+        }
+    }
+    bool used = false;
+    rc = batch_graph(ctx, mode, n30, n210, rp ? ro30.data() : nullptr, rp ? ro210.data() : nullptr, &used);
+    if (rc) return rc;
+    if (!used) {  // bucket lists: direct launches, re-run with larger lists if one overflowed
+        for (int attempt = 0;; ++attempt) {
+            if (attempt == 4) return fail(ctx, SIEVE_EDEVICE, "bucket lists overflowed repeatedly");
+            rc = launch_ranges(ctx, ctx->stream, prm, mode, ctx->lb, n30, &ctx->buckets, &ctx->cursors,
+                               rp ? ro30.data() : nullptr);
+            if (rc) return rc;
+            int of = 0;
+            rc = finish(ctx, ctx->lb, n30, &of);
+            if (rc) return rc;
+            if (!of) break;
+            ctx->buckets.slack *= 2;
+        }
+        if (n210) {
+            rc = launch_ranges210(ctx, ctx->stream, prm, ctx->lb210, n210, nullptr, rp ? ro210.data() : nullptr);
+            int of = 0;
+            if (!rc) rc = finish(ctx, ctx->lb210, n210, &of);
+            if (rc) return rc;
+        }
+    }
+    for (size_t k = 0; k < pos30.size(); ++k) counts[pos30[k]] = ctx->lb.h_acc[k];
+    for (size_t k = 0; k < pos210.size(); ++k) counts[pos210[k]] = ctx->lb210.h_acc[k];
     return SIEVE_OK;
 }
 
@@ -849,6 +1010,7 @@ void sieve_destroy(sieve_ctx *ctx) {
     cudaFree(ctx->cursors.d);
     cudaFree(ctx->mr.d);
     free_launch_buffers(ctx, ctx->lb);
+    free_launch_buffers(ctx, ctx->lb210);
     free_compact_scratch(ctx, ctx->cs);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -957,58 +1119,28 @@ int sieve_compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo, uint6
 
 int sieve_batch_count(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t m, uint64_t *counts,
                       uint32_t *const *bitmaps_dev) {
+    return sieve_batch_count_params(ctx, lo, hi, m, nullptr, counts, bitmaps_dev);
+}
+
+int sieve_batch_count_params(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t m,
+                             const sieve_range_params *params, uint64_t *counts, uint32_t *const *bitmaps_dev) {
     if (!ctx) return SIEVE_EINVAL;
     if (m == 0) return SIEVE_OK;
     if (!lo || !hi || !counts) return fail(ctx, SIEVE_EINVAL, "null array");
     for (size_t i = 0; i < m; ++i) {
         int rc = check_range(ctx, lo[i], hi[i]);
         if (rc) return rc;
+        if (params) {
+            const sieve_range_params &q = params[i];
+            if (q.seg_bytes && (q.seg_bytes < 1024 || q.seg_bytes > kMaxSegmentBytes || q.seg_bytes % 32))
+                return fail(ctx, SIEVE_EINVAL, "range segment bytes");
+            if (q.wheel && q.wheel != 30 && q.wheel != 210) return fail(ctx, SIEVE_EINVAL, "range wheel (30 or 210)");
+            if (q.mid_limit > (1u << 31)) return fail(ctx, SIEVE_EINVAL, "range mid limit");
+        }
     }
     int rc = set_device(ctx);
     if (rc) return rc;
-    rc = ensure_launch(ctx, m);
-    if (rc) return rc;
-    const int mode = bitmaps_dev ? kModeBitmap : ctx->params.wheel == 210 ? kModeCount210 : kModeCount;
-    auto plan = [&](size_t i) {
-        return mode == kModeCount210 ? plan_range210(ctx, lo[i], hi[i], w210_segment_words(ctx->params))
-                                     : plan_range(ctx, lo[i], hi[i], ctx->params.seg_bytes, mode,
-                                                  bitmaps_dev ? bitmaps_dev[i] : nullptr);
-    };
-    // Launch order (SIEVE_PARAM_BATCH_ORDER): as given, heaviest first, or heaviest
-    // and lightest alternating -- GPU forms of sieving the last blocks from both
-    // ends, since persistent CTAs take work items in launch order.  Estimated work
-    // of a range: every segment visits its n_use base primes (about 3 warp
-    // instructions each) and crosses 0.16 warp instructions per integer.
-    std::vector<uint32_t> &order = ctx->batch_order;
-    order.resize(m);
-    for (size_t i = 0; i < m; ++i) order[i] = (uint32_t)i;
-    if (ctx->params.batch_order) {
-        std::vector<double> cost(m);
-        for (size_t i = 0; i < m; ++i) {
-            const RangeDesc r = plan(i);
-            cost[i] = 3.0 * (double)r.nseg * r.n_use + 0.16 * (double)(hi[i] - lo[i]);
-        }
-        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
-        if (ctx->params.batch_order == 2) {  // heaviest, lightest, second heaviest, ...
-            std::vector<uint32_t> mixed;
-            mixed.reserve(m);
-            for (size_t a = 0, b = m; a < b;) {
-                mixed.push_back(order[a++]);
-                if (a < b) mixed.push_back(order[--b]);
-            }
-            order.swap(mixed);
-        }
-    }
-    for (size_t k = 0; k < m; ++k) ctx->lb.h_ranges()[k] = plan(order[k]);
-    bool used = false;
-    rc = batch_graph(ctx, mode, m, &used);
-    if (rc) return rc;
-    if (!used) {  // not reached for kModeCount210 (always captured)
-        rc = run_sync(ctx, ctx->params, mode, m);
-        if (rc) return rc;
-    }
-    for (size_t k = 0; k < m; ++k) counts[order[k]] = ctx->lb.h_acc[k];
-    return SIEVE_OK;
+    return batch_impl(ctx, lo, hi, m, params, counts, bitmaps_dev);
 }
 
 int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {

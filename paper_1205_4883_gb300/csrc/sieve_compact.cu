@@ -4,10 +4,9 @@
 // set bits of every tile, pass 2 scans the tile counts into tile offsets (one
 // CTA), pass 3 re-reads each tile and writes, for bit i of the bitmap, the
 // prime o0 + 2 i at its rank.  In passes 1 and 3 a CTA of 256 threads takes a
-// tile; warp w takes the tile's words [256 w, 256 w + 256) as eight chunks of
-// 32, lane l holding word 32 k + l of chunk k, so every load instruction reads
-// 128 contiguous bytes.  The primes of a chunk are ranked by a warp scan in
-// word order, gathered in shared memory and written out as one contiguous run.
+// tile and warp w the tile's words [256 w, 256 w + 256).  In pass 1 lane l
+// holds word 32 k + l of chunk k (every load instruction reads 128 contiguous
+// bytes); in pass 3 it holds eight consecutive words (k_emit).
 #include "internal.h"
 
 namespace gbs {
@@ -101,53 +100,70 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t *tile_counts,
     if (threadIdx.x == 0) *total = s_run;
 }
 
-// Primes a warp stages in shared memory per chunk before writing them out as
-// one contiguous run (a denser chunk is written directly).
-constexpr uint32_t kEmitStage = 512;
+// Primes a warp stages in shared memory before writing them out as one
+// contiguous run (a warp's 256 words hold more only near 0; then it writes
+// directly).
+constexpr uint32_t kEmitStage = 1024;
 
+// Pass 3.  Warp w of a CTA takes words [256 w, 256 w + 256) of the tile, lane l
+// the eight consecutive words 8 l .. 8 l + 7 of those (two 16-byte loads per
+// lane, so a load instruction reads 512 contiguous bytes).  One warp scan of the
+// lanes' popcounts ranks every prime of the warp's words; each lane writes its
+// primes, in order, into the warp's stage in shared memory, and the warp copies
+// the stage out as one contiguous run.  With total != null the list is written
+// only if it fits: *total (from k_tile_scan) + base_index <= cap; otherwise the
+// kernel writes nothing, so the host can launch it before it has read the total.
 template <typename T>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ bitmap, uint64_t nwords,
                                               const uint64_t *__restrict__ tile_offsets, uint64_t ntiles,
-                                              uint64_t o0, uint32_t base_index, T *__restrict__ out) {
+                                              uint64_t o0, uint32_t base_index, T *__restrict__ out,
+                                              const unsigned long long *total, uint64_t cap) {
     __shared__ uint32_t s_warp[8];
-    __shared__ T s_stage[8][kEmitStage];
+    extern __shared__ __align__(16) unsigned char s_dyn[];  // 8 stages of kEmitStage entries
+    if (total && *total + base_index > cap) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool vec = (reinterpret_cast<uintptr_t>(bitmap) & 15u) == 0;
+    T *const stage = reinterpret_cast<T *>(s_dyn) + (size_t)warp * kEmitStage;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t base = t * kCompactTileWords + 256ull * warp;
+        const uint64_t w0 = t * kCompactTileWords + 256ull * warp + 8ull * lane;  // this lane's first word
         uint32_t w[8];
+        if (vec && w0 + 8 <= nwords) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(bitmap + w0));
+            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(bitmap + w0) + 1);
+            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+            w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) w[k] = w0 + k < nwords ? __ldg(bitmap + w0 + k) : 0u;
+        }
         uint32_t c = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint64_t i = base + 32ull * k + lane;
-            w[k] = i < nwords ? __ldg(bitmap + i) : 0u;
-            c += __popc(w[k]);
-        }
-        c = warp_sum_u32(c);
-        if (lane == 0) s_warp[warp] = c;
+        for (int k = 0; k < 8; ++k) c += __popc(w[k]);
+        const uint32_t incl = warp_inclusive_scan_u32(c, lane);
+        const uint32_t n = __shfl_sync(0xffffffffu, incl, 31);  // primes in the warp's 256 words
+        if (lane == 0) s_warp[warp] = n;
         __syncthreads();
-        uint32_t before = 0;  // primes of the tile's earlier warps
-        for (int i = 0; i < warp; ++i) before += s_warp[i];
-        uint64_t chunk = base_index + tile_offsets[t] + before;  // rank of the chunk's first prime
+        uint64_t first = base_index + tile_offsets[t];  // rank of the warp's first prime
+        for (int i = 0; i < warp; ++i) first += s_warp[i];
+        uint64_t v = o0 + 64ull * w0;  // integer of bit 0 of the lane's first word
+        if (n <= kEmitStage) {
+            uint32_t j = incl - c;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t v = w[k], cv = __popc(v);
-            const uint32_t incl = warp_inclusive_scan_u32(cv, lane);
-            const uint32_t n = __shfl_sync(0xffffffffu, incl, 31);  // primes in the chunk
-            const uint64_t first = o0 + 64ull * (base + 32ull * k + lane);  // integer of the word's bit 0
-            if (n <= kEmitStage) {
-                T *stage = s_stage[warp];
-                uint32_t j = incl - cv;
-                for (uint32_t x = v; x; x &= x - 1) stage[j++] = (T)(first + 2ull * (uint32_t)(__ffs(x) - 1));
-                __syncwarp();
-                for (uint32_t i = lane; i < n; i += 32) out[chunk + i] = stage[i];
-                __syncwarp();
-            } else {
-                uint64_t pos = chunk + incl - cv;
-                for (uint32_t x = v; x; x &= x - 1) out[pos++] = (T)(first + 2ull * (uint32_t)(__ffs(x) - 1));
+            for (int k = 0; k < 8; ++k) {
+                for (uint32_t x = w[k]; x; x &= x - 1) stage[j++] = (T)(v + 2ull * (uint32_t)(__ffs(x) - 1));
+                v += 64;
             }
-            chunk += n;
+            __syncwarp();
+            for (uint32_t i = lane; i < n; i += 32) out[first + i] = stage[i];
+        } else {
+            uint64_t pos = first + incl - c;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                for (uint32_t x = w[k]; x; x &= x - 1) out[pos++] = (T)(v + 2ull * (uint32_t)(__ffs(x) - 1));
+                v += 64;
+            }
         }
-        __syncthreads();
+        __syncthreads();  // s_warp and the stages are reused by the next tile
     }
 }
 
@@ -168,15 +184,38 @@ cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint
 }
 
 cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets, uint64_t ntiles,
-                        uint64_t o0, uint32_t base_index, void *out, int out64, int grid, cudaStream_t stream) {
+                        uint64_t o0, uint32_t base_index, void *out, int out64, int grid, cudaStream_t stream,
+                        const unsigned long long *total, uint64_t cap) {
     if (ntiles == 0) return cudaSuccess;
     const unsigned g = (unsigned)(ntiles < (uint64_t)grid ? ntiles : (uint64_t)grid);
+    if (out64) {
+        const int smem = 8 * kEmitStage * sizeof(uint64_t);  // 64 KiB: above the default 48 KiB
+        cudaError_t e = cudaFuncSetAttribute(k_emit<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        k_emit<uint64_t><<<g, 256, smem, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
+                                                   static_cast<uint64_t *>(out), total, cap);
+    } else {
+        const int smem = 8 * kEmitStage * sizeof(uint32_t);
+        k_emit<uint32_t><<<g, 256, smem, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
+                                                   static_cast<uint32_t *>(out), total, cap);
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+// out[0] = 2 when the list fits: *total + 1 <= cap.
+template <typename T>
+__global__ void k_put_two_if_fits(T *out, const unsigned long long *total, uint64_t cap) {
+    if (*total + 1 <= cap) out[0] = (T)2;
+}
+}  // namespace
+
+cudaError_t launch_put_two_if_fits(void *out, int out64, const unsigned long long *total, uint64_t cap,
+                                   cudaStream_t stream) {
     if (out64)
-        k_emit<uint64_t><<<g, 256, 0, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
-                                                static_cast<uint64_t *>(out));
+        k_put_two_if_fits<uint64_t><<<1, 1, 0, stream>>>(static_cast<uint64_t *>(out), total, cap);
     else
-        k_emit<uint32_t><<<g, 256, 0, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
-                                                static_cast<uint32_t *>(out));
+        k_put_two_if_fits<uint32_t><<<1, 1, 0, stream>>>(static_cast<uint32_t *>(out), total, cap);
     return cudaGetLastError();
 }
 

@@ -438,14 +438,15 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
 
     init_tables(tab);
     const int tid = threadIdx.x, lane = tid & 31;
-    const uint32_t S = P.seg_bytes, C = P.chunk_segs;
+    const uint32_t C = P.chunk_segs;
     if (tid < 32) {  // cumulative costs of the medium groups (read after the next barrier)
         const uint32_t ng = P.mid_end > P.small_end ? (P.mid_end - P.small_end + 31) / 32 : 0;
         const uint32_t G = ng <= kMidGroups ? ng : 0;
         uint32_t run = 0;
         for (uint32_t g0 = 0; g0 < G; g0 += 32) {
             const uint32_t g = g0 + lane;
-            const uint32_t c = g < G ? kMidSetup + 8u * S / __ldg(P.primes + P.small_end + 32u * g) : 0u;
+            const uint32_t c =
+                g < G ? kMidSetup + 8u * P.seg_bytes / __ldg(P.primes + P.small_end + 32u * g) : 0u;
             const uint32_t incl = warp_inclusive_scan(c, lane);
             if (g < G) s_midW[g + 1] = run + incl;
             run += __shfl_sync(0xffffffffu, incl, 31);
@@ -476,6 +477,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
         if (item >= P.n_items) break;
         const RangeDesc &rd = P.ranges[s_range];
         const uint32_t range_id = s_range;
+        const uint32_t S = rd.seg_bytes;  // this range's segment size (<= P.seg_bytes)
         // this item: segments [s0, s0 + nchunk) of the range
         const uint64_t s0 = (item - rd.item_first) * C;
         const uint32_t nchunk = (uint32_t)(rd.nseg - s0 < C ? rd.nseg - s0 : C);
@@ -491,7 +493,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
 
         // 0. bucket fill: every bucket prime with a multiple in this chunk
         //    appends its hits to the chunk's per-segment lists (in HBM)
-        const bool use_buckets = P.bucket_first < n_range;
+        const bool use_buckets = rd.bucket_first < n_range;
         if (use_buckets) {
             if (tid < 32) {
                 const uint64_t E = (uint64_t)(30 * (Bs + (int64_t)chunk_bytes));
@@ -504,7 +506,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             // the chunk the warp counts its lanes' hits, reserves room with one
             // shared-memory atomic, and each lane writes its hits contiguously
             const uint32_t nb = s_nbucket;
-            for (uint32_t base = P.bucket_first + (tid & ~31u); base < nb; base += blockDim.x) {
+            for (uint32_t base = rd.bucket_first + (tid & ~31u); base < nb; base += blockDim.x) {
                 const uint32_t i = base + lane;
                 const bool valid = i < nb;
                 const uint32_t p = valid ? __ldg(P.primes + i) : 1u;
@@ -631,7 +633,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             // a range on the Miller-Rabin path is sieved with the primes below 2^16 only
             const uint32_t n_seg = rd.mr && P.mr_end < s_nseg ? P.mr_end : s_nseg;
             // primes crossed here (not through the buckets): [8, n_use)
-            const uint32_t n_use = use_buckets && P.bucket_first < n_seg ? P.bucket_first : n_seg;
+            const uint32_t n_use = use_buckets && rd.bucket_first < n_seg ? rd.bucket_first : n_seg;
             const uint32_t small_end = P.small_end < n_use ? P.small_end : n_use;
             const uint32_t n_small8 = (small_end > small_first ? small_end - small_first : 0) * 8;
 
@@ -640,7 +642,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             //     w-th 1/32 of the cumulative cost, so a heavy group (small primes,
             //     many hits) is shared by several warps, each crossing it over its
             //     own part of the segment.
-            const uint32_t mid_end = P.mid_end < n_use ? P.mid_end : n_use;
+            const uint32_t mid_end = rd.mid_end < n_use ? rd.mid_end : n_use;
             const uint32_t Lw = L >> 2;
             {
                 // G > 0: warp w takes the cost interval [x0, x1); G = 0 (too many

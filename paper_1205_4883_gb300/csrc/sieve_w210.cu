@@ -115,7 +115,7 @@ k_sieve210(const SieveLaunch *__restrict__ Pg, const W210Tables *__restrict__ T,
     if (threadIdx.x == 0) P = *Pg;
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31;
-    const uint32_t Sw = P.seg_bytes / 4, Sg = Sw / 3 * 2, C = P.chunk_segs;
+    const uint32_t C = P.chunk_segs;
 
     for (;;) {
         if (tid == 0) {
@@ -135,6 +135,7 @@ k_sieve210(const SieveLaunch *__restrict__ Pg, const W210Tables *__restrict__ T,
         if (item >= P.n_items) break;
         const uint32_t range_id = s_range;
         const RangeDesc &rd = P.ranges[range_id];
+        const uint32_t Sw = rd.seg_bytes / 4, Sg = Sw / 3 * 2;  // this range's segment (<= the launch's)
         const uint64_t s0 = (item - rd.item_first) * C;
         const uint32_t nchunk = (uint32_t)(rd.nseg - s0 < C ? rd.nseg - s0 : C);
         const uint32_t n_range = rd.n_use;
@@ -170,7 +171,7 @@ k_sieve210(const SieveLaunch *__restrict__ Pg, const W210Tables *__restrict__ T,
             __syncthreads();
             const uint32_t n_use = s_nseg;
             const uint32_t small_end = P.small_end < n_use ? P.small_end : n_use;
-            const uint32_t mid_end = P.mid_end < n_use ? P.mid_end : n_use;
+            const uint32_t mid_end = rd.mid_end < n_use ? rd.mid_end : n_use;
 
             // 2a. medium primes [small_end, mid_end): one lane per prime, the
             //     warp taking 32 consecutive primes.  Each class progression

@@ -347,15 +347,73 @@ def test_batch_with_bitmaps(sv):
             assert np.array_equal(bms[i][:nw].cpu().numpy().view(np.uint32), oracle.bitmap(a, b)), i
 
 
+def _random_range_params(m, seed, bitmaps=False):
+    from paper_1205_4883_gb300 import autotune
+    from paper_1205_4883_gb300.workloads import SplitMix64
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(m):
+        q = {}
+        for f, cands in autotune.CANDIDATES.items():
+            q[f] = cands[rng.next() % len(cands)]
+        if bitmaps:
+            q["wheel"] = 30 if rng.next() % 2 else 0
+        if rng.next() % 4 == 0:
+            q["seg_bytes"] = 1024 + 32 * (rng.next() % 7000)
+        out.append(q)
+    return out
+
+
+def test_batch_per_range_parameters_do_not_change_results(sv):
+    # the 4096-interval batch with every range's segment bytes, wheel, bucket limit, tier
+    # limit and Miller-Rabin threshold drawn at random, in one launch: every count
+    # against the oracle
+    los, his = batch_intervals(4096, seed=1205)
+    params = _random_range_params(4096, seed=7)
+    assert sv.batch_count_params(los, his, params) == oracle_pool.counts(los, his)
+
+
+def test_batch_per_range_parameters_with_bitmaps(sv):
+    # bitmap mode (mod-30 wheel only): counts and every word of every bitmap
+    los, his = batch_intervals(512, seed=99, lo_exp=(3, 14), w_exp=(2, 7))
+    params = _random_range_params(512, seed=8, bitmaps=True)
+    nws = [gb.sieve_bitmap_words(a, b) for a, b in zip(los, his)]
+    offs = np.concatenate([[0], np.cumsum(nws)]).astype(np.int64)
+    store = torch.zeros(int(offs[-1]) + 1, dtype=torch.int32, device="cuda")
+    ptrs = [store.data_ptr() + 4 * int(offs[i]) for i in range(512)]
+    counts = sv.batch_count_params(los, his, params, ptrs)
+    host = store.cpu().numpy().view(np.uint32)
+    assert counts == oracle_pool.counts(los, his)
+    bad = [i for i, ok in enumerate(oracle_pool.pmap(
+        lambda i: np.array_equal(host[offs[i]:offs[i + 1]], oracle.bitmap(los[i], his[i])), range(512))) if not ok]
+    assert bad == []
+
+
+def test_batch_per_range_parameter_errors(sv):
+    los, his = [10**9, 10**10], [10**9 + 1000, 10**10 + 1000]
+    for bad in ({"seg_bytes": 1000}, {"seg_bytes": 229376 + 32}, {"wheel": 60}):
+        with pytest.raises(gb.SieveError) as e:
+            sv.batch_count_params(los, his, [bad, {}])
+        assert e.value.code == gb.SIEVE_EINVAL
+    bm = [torch.zeros(64, dtype=torch.int32, device="cuda") for _ in range(2)]
+    with pytest.raises(gb.SieveError) as e:
+        sv.batch_count_params(los, his, [{"wheel": 210}, {}], bm)
+    assert e.value.code == gb.SIEVE_EINVAL
+    # all fields 0: the context's parameters, as sieve_batch_count
+    assert sv.batch_count_params(los, his, [{}, {}]) == sv.batch_count(los, his)
+
+
 def test_batch_tuned_equals_untuned(sv):
     from paper_1205_4883_gb300 import autotune
-    los, his = batch_intervals(300, seed=3, lo_exp=(2, 13), w_exp=(1, 7))
-    table = {"classes": {"0/0": {"segment_bytes": 32768, "small_limit": 256},
-                         "1/1": {"segment_bytes": 65536, "threads": 512},
-                         "2/2": {"bucket_limit": 0, "chunk_segments": 4}}}
-    assert sv.batch_count_tuned(los, his, table) == sv.batch_count(los, his)
-    assert sv.get_param(gb.SIEVE_PARAM_SEGMENT_BYTES) == 229376  # restored
-    assert autotune.class_key(los[0], his[0]) in {f"{a}/{b}" for a in range(3) for b in range(4)}
+    los, his = batch_intervals(600, seed=3, lo_exp=(2, 14), w_exp=(1, 7))
+    table = {"classes": {"0/0": {"seg_bytes": 32768, "mid_limit": 4096},
+                         "1/1": {"wheel": 210, "seg_bytes": 65536},
+                         "2/2": {"bucket_limit": 229376},
+                         "4/2": {"mr_percent": 100},
+                         "3/1": {"wheel": 210}}}
+    assert sv.batch_count_tuned(los, his, table) == sv.batch_count(los, his) == oracle_pool.counts(los, his)
+    assert sv.get_param(gb.SIEVE_PARAM_SEGMENT_BYTES) == 229376  # the context is untouched
+    assert {autotune.class_key(a, b) for a, b in zip(los, his)} >= {"0/0", "1/1", "2/2"}
 
 
 @pytest.mark.parametrize("lo,hi", [(0, 10**10), (99 * 10**10, 10**12), (10**9 - 5, 10**9 + 4 * 10**9),
