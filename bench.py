@@ -623,7 +623,7 @@ def run_outputs(args, lo, hi, name, with_count):
     return 0
 
 
-def served_measure(rates, requests=0, cpu=True):
+def served_measure(rates, requests=0, cpu=True, **server_kw):
     """A seeded Poisson stream (80% count, 20% list; lo log-uniform in [0, 1e12], width
     log-uniform in [1e4, 1e9]) at each offered rate through the request server:
     p50/p99 latency (submit to result on the host) and integers/s, against the plain
@@ -642,39 +642,33 @@ def served_measure(rates, requests=0, cpu=True):
             n = requests or int(min(10000, max(300, rate)))
             reqs = served_stream(rate=rate, n=n, seed=1205)
             all_reqs.append(reqs)
-            with gb.Server(sv, max_device_bytes=16 << 30) as srv:
+            with gb.Server(sv, max_device_bytes=16 << 30, **server_kw) as srv:
                 tickets = queue.Queue()
                 lat, errors = [], []
 
-                def collect():  # picks up finished results in any order and releases them (frees slots)
-                    outstanding, closed = [], False
+                kinds = {}
+
+                def collect():  # drains the completion queue, reads each result and releases it (frees slots)
+                    expected, done = None, 0
                     deadline = time.perf_counter() + 900
-                    while (not closed or outstanding) and time.perf_counter() < deadline:
+                    while (expected is None or done < expected) and time.perf_counter() < deadline:
                         while True:
                             try:
                                 t = tickets.get_nowait()
                             except queue.Empty:
                                 break
                             if t is None:
-                                closed = True
-                            else:
-                                outstanding.append(t)
-                        still = []
-                        for t in outstanding:
+                                expected = len(kinds)
+                        for t in srv.wait_any(4096, timeout_us=2000):
                             rc, res = srv.poll(t, timeout_us=0, copy_primes=False)
-                            if rc == gb.SIEVE_ETIMEOUT:
-                                still.append(t)
-                                continue
                             if res["status"] != gb.SIEVE_OK:
                                 errors.append(res)
                             else:
-                                lat.append(res["latency_us"])
+                                lat.append((res["latency_us"], t))
                             srv.release(t)
-                        if len(still) == len(outstanding):
-                            time.sleep(0.0002)
-                        outstanding = still
-                    if outstanding:
-                        errors.append(f"{len(outstanding)} requests unfinished after 900 s")
+                            done += 1
+                    if expected is None or done < expected:
+                        errors.append(f"{(expected or 0) - done} requests unfinished after 900 s")
 
                 th = threading.Thread(target=collect)
                 th.start()
@@ -695,17 +689,27 @@ def served_measure(rates, requests=0, cpu=True):
                         rejected += 1
                         time.sleep(0.0005)
                         rc, t = srv.submit(r.lo, r.hi, kind)
+                    kinds[t] = r.kind
                     tickets.put(t)
                 tickets.put(None)
                 th.join()
                 wall = time.perf_counter() - t0
+                st = srv.stats()
                 if errors:
                     raise RuntimeError(f"served requests failed: {errors[:3]}")
             ints = sum(r.hi - r.lo for r in reqs)
+            lat_all = [x for x, _ in lat]
+            by_kind = {}
+            for kd in ("count", "list"):
+                xs = [x for x, t in lat if kinds[t] == kd]
+                if xs:
+                    by_kind[kd] = {"n": len(xs), "p50_ms": float(np.percentile(xs, 50)) / 1e3,
+                                   "p99_ms": float(np.percentile(xs, 99)) / 1e3}
             results.append({"offered_req_s": rate, "requests": len(reqs), "integers_per_s": ints / wall,
-                            "p50_ms": float(np.percentile(lat, 50)) / 1e3,
-                            "p99_ms": float(np.percentile(lat, 99)) / 1e3,
-                            "wall_s": wall, "busy_retries": rejected})
+                            "p50_ms": float(np.percentile(lat_all, 50)) / 1e3,
+                            "p99_ms": float(np.percentile(lat_all, 99)) / 1e3, "by_kind": by_kind,
+                            "wall_s": wall, "busy_retries": rejected, "ticks": st["ticks"],
+                            "segments": st["segments"], "tick_gpu_ms": st["tick_gpu_ms"]})
     best_i = max(range(len(results)), key=lambda i: results[i]["integers_per_s"])
     best = results[best_i]
     reqs = all_reqs[best_i]

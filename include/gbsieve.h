@@ -220,6 +220,11 @@ typedef struct {
     uint32_t max_requests;     /* requests admitted and not yet released (0: 1024) */
     uint32_t tick_segments;    /* segments per scheduling tick (0: 4 x SMs) */
     uint64_t max_device_bytes; /* device memory for list requests (0: 4 GiB) */
+    uint32_t serial_ticks;     /* 1: both tick slots on one stream, so a tick's kernels start only
+                                  when the previous tick's have ended; 0 (default): one stream per
+                                  slot, so the next tick's CTAs fill the SMs the previous tick's
+                                  last segments leave idle */
+    uint32_t reserved;
 } sieve_server_cfg;
 
 typedef struct {
@@ -245,6 +250,9 @@ typedef struct {
     uint32_t in_flight;     /* admitted, not yet completed */
     uint32_t reserved;
     uint64_t device_bytes_reserved;
+    uint64_t segments;      /* segments sieved by the ticks so far */
+    double tick_gpu_ms;     /* sum over ticks of the GPU time from a tick's first launch to its
+                               last copy (CUDA events); ticks on two streams may overlap */
 } sieve_server_counters;
 
 /* Start a server on ctx (cfg may be NULL for defaults).  ctx must outlive it. */
@@ -258,6 +266,14 @@ int sieve_server_submit(sieve_server *srv, const sieve_req *req, uint64_t *ticke
  * SIEVE_ETIMEOUT if it is not ready by then, SIEVE_ENOENT for an unknown or
  * released ticket.  May be called again after a timeout or a success. */
 int sieve_server_poll(sieve_server *srv, uint64_t ticket, sieve_result *res, int64_t timeout_us);
+
+/* Completion queue: wait up to timeout_us microseconds (< 0: no limit) until at
+ * least one request has completed and not yet been reported here, then write up
+ * to cap such tickets, in completion order, to tickets[0 .. *n).  Each completed
+ * request is reported once (whether or not it was also polled), so a caller can
+ * collect and release results without polling every ticket.  SIEVE_ETIMEOUT
+ * (*n = 0) if none completed in time. */
+int sieve_server_wait_any(sieve_server *srv, uint64_t *tickets, size_t cap, size_t *n, int64_t timeout_us);
 
 /* Forget a completed request and free its result (SIEVE_EBUSY if not done). */
 int sieve_server_release(sieve_server *srv, uint64_t ticket);

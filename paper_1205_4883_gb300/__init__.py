@@ -63,7 +63,7 @@ class sieve_info(ctypes.Structure):
 
 class sieve_server_cfg(ctypes.Structure):
     _fields_ = [("max_requests", ctypes.c_uint32), ("tick_segments", ctypes.c_uint32),
-                ("max_device_bytes", _u64)]
+                ("max_device_bytes", _u64), ("serial_ticks", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class sieve_req(ctypes.Structure):
@@ -78,7 +78,7 @@ class sieve_result(ctypes.Structure):
 class sieve_server_counters(ctypes.Structure):
     _fields_ = [("submitted", _u64), ("completed", _u64), ("rejected", _u64), ("ticks", _u64),
                 ("integers", _u64), ("in_flight", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("device_bytes_reserved", _u64)]
+                ("device_bytes_reserved", _u64), ("segments", _u64), ("tick_gpu_ms", ctypes.c_double)]
 
 
 class sieve_range_params(ctypes.Structure):
@@ -118,6 +118,7 @@ _SIGS = {
     "sieve_server_submit": (_int, [_vp, ctypes.POINTER(sieve_req), _pu64]),
     "sieve_server_poll": (_int, [_vp, _u64, ctypes.POINTER(sieve_result), _i64]),
     "sieve_server_release": (_int, [_vp, _u64]),
+    "sieve_server_wait_any": (_int, [_vp, _pu64, _sz, ctypes.POINTER(_sz), _i64]),
     "sieve_server_stats": (_int, [_vp, ctypes.POINTER(sieve_server_counters)]),
     "sieve_server_destroy": (None, [_vp]),
     "sieve_selftest_wait": (_int, [_vp, _int, ctypes.c_uint32, ctypes.POINTER(_int)]),
@@ -381,8 +382,9 @@ def sieve_stream(ctx: int) -> int:
     return load_library().sieve_stream(ctx) or 0
 
 
-def sieve_server_create(ctx: int, max_requests: int = 0, tick_segments: int = 0, max_device_bytes: int = 0) -> int:
-    cfg = sieve_server_cfg(max_requests, tick_segments, max_device_bytes)
+def sieve_server_create(ctx: int, max_requests: int = 0, tick_segments: int = 0, max_device_bytes: int = 0,
+                        serial_ticks: bool = False) -> int:
+    cfg = sieve_server_cfg(max_requests, tick_segments, max_device_bytes, 1 if serial_ticks else 0, 0)
     h = _vp()
     rc = load_library().sieve_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h))
     _check(ctx, rc)
@@ -417,6 +419,16 @@ def sieve_server_poll(srv: int, ticket: int, timeout_us: int = -1, copy_primes: 
     return rc, out
 
 
+def sieve_server_wait_any(srv: int, cap: int = 1024, timeout_us: int = -1):
+    """Tickets of requests completed since the last call (up to cap); [] on timeout."""
+    import numpy as np
+    out = np.zeros(max(cap, 1), dtype=np.uint64)
+    n = _sz()
+    rc = load_library().sieve_server_wait_any(srv, out.ctypes.data_as(_pu64), cap, ctypes.byref(n), timeout_us)
+    _check(0, rc, allow=(SIEVE_ETIMEOUT,))
+    return out[:n.value].tolist()
+
+
 def sieve_server_release(srv: int, ticket: int) -> int:
     rc = load_library().sieve_server_release(srv, ticket)
     _check(0, rc, allow=(SIEVE_EBUSY, SIEVE_ENOENT))
@@ -436,9 +448,10 @@ def sieve_server_destroy(srv: int) -> None:
 class Server:
     """A continuous-batching request server on a Sieve context."""
 
-    def __init__(self, sieve: "Sieve", max_requests: int = 0, tick_segments: int = 0, max_device_bytes: int = 0):
+    def __init__(self, sieve: "Sieve", max_requests: int = 0, tick_segments: int = 0, max_device_bytes: int = 0,
+                 serial_ticks: bool = False):
         self.sieve = sieve  # keeps the context alive
-        self.srv = sieve_server_create(sieve.ctx, max_requests, tick_segments, max_device_bytes)
+        self.srv = sieve_server_create(sieve.ctx, max_requests, tick_segments, max_device_bytes, serial_ticks)
 
     def submit(self, lo, hi, kind=SIEVE_REQ_COUNT):
         return sieve_server_submit(self.srv, lo, hi, kind)
@@ -448,6 +461,9 @@ class Server:
 
     def release(self, ticket):
         return sieve_server_release(self.srv, ticket)
+
+    def wait_any(self, cap=1024, timeout_us=-1):
+        return sieve_server_wait_any(self.srv, cap, timeout_us)
 
     def stats(self):
         return sieve_server_stats(self.srv)

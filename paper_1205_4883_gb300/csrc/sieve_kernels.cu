@@ -646,8 +646,12 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             const uint32_t Lw = L >> 2;
             {
                 // G > 0: warp w takes the cost interval [x0, x1); G = 0 (too many
-                // groups for the table): warp w takes groups w, w + 32, ... whole
-                const uint32_t G = s_midG, warp = tid >> 5, nwarps = blockDim.x >> 5;
+                // groups for the table): warp w takes groups w, w + 32, ... whole.
+                // The cost is dealt over the groups this segment has (those below
+                // mid_end, which this range's tier limit or p^2 may put before the
+                // table's end), so no warp is dealt groups that are not crossed here.
+                const uint32_t Gs = mid_end > P.small_end ? (mid_end - P.small_end + 31) / 32 : 0;
+                const uint32_t G = s_midG < Gs ? s_midG : Gs, warp = tid >> 5, nwarps = blockDim.x >> 5;
                 const uint32_t T = s_midW[G];
                 const uint32_t x0 = (uint32_t)((uint64_t)T * warp / nwarps);
                 const uint32_t x1 = (uint32_t)((uint64_t)T * (warp + 1) / nwarps);

@@ -65,7 +65,9 @@ struct Run {
 struct Tick {
     LaunchBuffers lb[2];  // [0] count-mode runs, [1] bitmap-mode runs
     std::vector<Run> runs[2];
-    cudaEvent_t ev = nullptr;
+    cudaStream_t stream = nullptr;  // the stream this tick slot launches on
+    cudaEvent_t ev0 = nullptr, ev = nullptr;  // around the tick's work (timing events)
+    uint64_t segments = 0;
     bool busy = false;
 };
 
@@ -125,7 +127,8 @@ struct sieve_server {
     sieve_ctx *owner = nullptr;
     sieve_ctx *view = nullptr;  // private context view: borrowed resident state, own buffers
     sieve_server_cfg cfg{};
-    cudaStream_t stream = nullptr;   // sieve ticks
+    cudaStream_t stream = nullptr;   // sieve ticks (slot 0, and slot 1 with serial_ticks)
+    cudaStream_t stream2 = nullptr;  // slot 1 of the ticks unless serial_ticks
     Tick ticks[2];
     int next_tick = 0;
     Arena arena;
@@ -139,6 +142,7 @@ struct sieve_server {
 
     std::map<uint64_t, std::unique_ptr<Req>> reqs;
     std::deque<Req *> active;  // admitted, segments left to schedule or in flight
+    std::deque<uint64_t> done_q;  // tickets completed and not yet reported by sieve_server_wait_any
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread th;
@@ -172,6 +176,7 @@ void complete(sieve_server *srv, Req *r, int status) {
     r->status = status;
     r->latency_us = std::chrono::duration<double, std::micro>(Clock::now() - r->t_submit).count();
     r->done = true;
+    srv->done_q.push_back(r->ticket);
     srv->st.completed++;
     srv->st.integers += r->hi - r->lo;
     srv->st.in_flight--;
@@ -240,6 +245,9 @@ void harvest(sieve_server *srv, Tick &t) {
     }
     t.busy = false;
     srv->st.ticks++;
+    srv->st.segments += t.segments;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.ev0, t.ev) == cudaSuccess) srv->st.tick_gpu_ms += ms;
     if (any) srv->cv_done.notify_all();
 }
 
@@ -286,15 +294,18 @@ int launch_tick(sieve_server *srv, Tick &t) {
         budget -= take;
     }
     if (!m[0] && !m[1]) return 0;
+    t.segments = srv->cfg.tick_segments - budget;
+    cudaError_t e = cudaEventRecord(t.ev0, t.stream);
+    if (e != cudaSuccess) return cuda_fail(srv->view, e, "tick event");
     for (int mode = 0; mode < 2; ++mode) {
         if (!m[mode]) continue;
-        int rc = launch_ranges(srv->view, srv->stream, srv->view->params, mode, t.lb[mode], m[mode], nullptr);
+        int rc = launch_ranges(srv->view, t.stream, srv->view->params, mode, t.lb[mode], m[mode], nullptr);
         if (rc) return rc;
-        cudaError_t e = cudaMemcpyAsync(t.lb[mode].h_acc, t.lb[mode].d_acc + 1, m[mode] * sizeof(unsigned long long),
-                                        cudaMemcpyDeviceToHost, srv->stream);
+        e = cudaMemcpyAsync(t.lb[mode].h_acc, t.lb[mode].d_acc + 1, m[mode] * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, t.stream);
         if (e != cudaSuccess) return cuda_fail(srv->view, e, "tick copy");
     }
-    cudaError_t e = cudaEventRecord(t.ev, srv->stream);
+    e = cudaEventRecord(t.ev, t.stream);
     if (e != cudaSuccess) return cuda_fail(srv->view, e, "tick event");
     t.busy = true;
     return 1;
@@ -395,12 +406,20 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server streams"));
     v->stream = srv->stream;
-    for (Tick &t : srv->ticks) {
+    // the Miller-Rabin path keeps raw words in one scratch of the view, which two
+    // ticks in flight would share: the server sieves every segment in full
+    v->params.mr_percent = 0;
+    if (!srv->cfg.serial_ticks) e = cudaStreamCreateWithFlags(&srv->stream2, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server streams"));
+    for (int k = 0; k < 2; ++k) {
+        Tick &t = srv->ticks[k];
+        t.stream = k == 1 && srv->stream2 ? srv->stream2 : srv->stream;
         for (auto &lb : t.lb) {
             int rc = alloc_launch_buffers(v, lb, srv->cfg.max_requests);
             if (rc) return bail(rc);
         }
-        e = cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming);
+        e = cudaEventCreate(&t.ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&t.ev);
         if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server event"));
     }
     e = cudaMalloc(&srv->arena.base, srv->cfg.max_device_bytes);
@@ -494,6 +513,26 @@ int sieve_server_poll(sieve_server *srv, uint64_t ticket, sieve_result *res, int
     return SIEVE_OK;
 }
 
+int sieve_server_wait_any(sieve_server *srv, uint64_t *tickets, size_t cap, size_t *n, int64_t timeout_us) {
+    if (!srv || !n || (!tickets && cap)) return SIEVE_EINVAL;
+    *n = 0;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto ready = [&] { return !srv->done_q.empty(); };
+    if (!ready()) {
+        if (timeout_us < 0)
+            srv->cv_done.wait(lk, ready);
+        else if (!srv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
+            return SIEVE_ETIMEOUT;
+    }
+    size_t k = 0;
+    while (k < cap && !srv->done_q.empty()) {
+        tickets[k++] = srv->done_q.front();
+        srv->done_q.pop_front();
+    }
+    *n = k;
+    return SIEVE_OK;
+}
+
 int sieve_server_release(sieve_server *srv, uint64_t ticket) {
     if (!srv) return SIEVE_EINVAL;
     std::lock_guard<std::mutex> lk(srv->mu);
@@ -530,8 +569,10 @@ void sieve_server_destroy(sieve_server *srv) {
     if (srv->view) {
         cudaSetDevice(srv->view->device);
         if (srv->stream) cudaStreamSynchronize(srv->stream);
+        if (srv->stream2) cudaStreamSynchronize(srv->stream2);
         for (Tick &t : srv->ticks) {
             for (auto &lb : t.lb) free_launch_buffers(srv->view, lb);
+            if (t.ev0) cudaEventDestroy(t.ev0);
             if (t.ev) cudaEventDestroy(t.ev);
         }
         for (Finisher &f : srv->fin) free_compact_scratch(srv->view, f.cs);
@@ -546,6 +587,7 @@ void sieve_server_destroy(sieve_server *srv) {
     srv->reqs.clear();  // results in the host arena die with it
     if (srv->host_arena.base) cudaFreeHost(srv->host_arena.base);
     if (srv->stream) cudaStreamDestroy(srv->stream);
+    if (srv->stream2) cudaStreamDestroy(srv->stream2);
     delete srv;
 }
 

@@ -25,9 +25,11 @@ def sv():
     s.close()
 
 
-def test_mixed_stream_equals_alone(sv):
+@pytest.mark.parametrize("serial", [False, True])
+def test_mixed_stream_equals_alone(sv, serial):
+    # ticks on two streams (overlapping) or on one: the same results
     reqs = served_stream(rate=1000.0, n=120, seed=1205, w_exp=(4, 8))
-    with gb.Server(sv, tick_segments=300) as srv:
+    with gb.Server(sv, tick_segments=300, serial_ticks=serial) as srv:
         tickets = []
         for r in reqs:
             kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
@@ -42,6 +44,7 @@ def test_mixed_stream_equals_alone(sv):
             assert srv.release(t) == gb.SIEVE_OK
         st = srv.stats()
         assert st["completed"] == len(reqs) and st["in_flight"] == 0
+        assert st["segments"] >= len(reqs) and st["tick_gpu_ms"] > 0 and st["ticks"] > 0
     for r, res in zip(reqs, results):
         alone = sv.count(r.lo, r.hi)
         assert res["count"] == alone, (r.lo, r.hi)
@@ -126,4 +129,30 @@ def test_list_results_beyond_the_pinned_arena(sv):
             assert res["count"] == len(want) == oracle.count(lo, hi)
             assert np.array_equal(res["primes"], want), (lo, hi)
         for t in tickets:
+            assert srv.release(t) == gb.SIEVE_OK
+
+
+def test_completion_queue_reports_each_request_once(sv):
+    # sieve_server_wait_any: every admitted request is reported exactly once, whether or
+    # not it was polled first, and results read after it are the requests' own
+    reqs = served_stream(rate=5000.0, n=200, seed=4, w_exp=(4, 7))
+    with gb.Server(sv, tick_segments=200) as srv:
+        want = {}
+        for i, r in enumerate(reqs):
+            kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
+            rc, t = srv.submit(r.lo, r.hi, kind)
+            assert rc == gb.SIEVE_OK
+            want[t] = r
+            if i == 10:  # one request polled before it is collected
+                rc, _ = srv.poll(t, timeout_us=60_000_000)
+                assert rc == gb.SIEVE_OK
+        seen = []
+        deadline = time.time() + 120
+        while len(seen) < len(reqs) and time.time() < deadline:
+            seen += srv.wait_any(64, timeout_us=100_000)
+        assert sorted(seen) == sorted(want)
+        assert srv.wait_any(8, timeout_us=1000) == []  # nothing left to report
+        for t in seen:
+            rc, res = srv.poll(t, timeout_us=0, copy_primes=False)
+            assert rc == gb.SIEVE_OK and res["count"] == oracle.count(want[t].lo, want[t].hi)
             assert srv.release(t) == gb.SIEVE_OK
