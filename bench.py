@@ -36,9 +36,14 @@ UNITS = 10**12                     # integers per rank per step
 METRIC = "integers sieved/s"
 # DRAM bytes (read + write) of one k_sieve<0> launch on this workload, from
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass, full launch);
-# reported only while the kernel source is the one it was measured on.
-TRAFFIC = {"kernel_sha256_16": "9f0b40c125b536dd", "bytes": 27.76e6 + 209.36e6}
-WORKLOAD = "pi(10^12): count primes in [0, 10^12), one range, count-only, mod-30 wheel + pattern of 7..19"
+# reported only while the kernel source AND the launch parameters are the ones
+# it was measured with (both are part of the key).
+TRAFFIC = {"key": None, "bytes": None}
+WORKLOAD = "pi(10^12): count primes in [0, 10^12), one range, count-only, mod-30 wheel + pre-sieved patterns"
+# the launch parameters that shape the kernel's memory traffic
+TRAFFIC_PARAMS = ("SIEVE_PARAM_SEGMENT_BYTES", "SIEVE_PARAM_THREADS", "SIEVE_PARAM_SMALL_LIMIT",
+                  "SIEVE_PARAM_CTAS_PER_SM", "SIEVE_PARAM_CHUNK_SEGMENTS", "SIEVE_PARAM_BUCKET_LIMIT",
+                  "SIEVE_PARAM_CURSOR_MB", "SIEVE_PARAM_MID_LIMIT", "SIEVE_PARAM_PRESIEVE")
 
 
 def _dist():
@@ -48,14 +53,23 @@ def _dist():
     return ws, rank, local
 
 
-def _traffic():
+def traffic_key(sv):
+    """SHA-256 prefix of the count kernel's source and of the launch parameters."""
     import hashlib
+    import paper_1205_4883_gb300 as gb
     src = os.path.join(ROOT, "paper_1205_4883_gb300", "csrc", "sieve_kernels.cu")
+    h = hashlib.sha256()
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h.update(open(src, "rb").read())
     except OSError:
         return None
-    return TRAFFIC["bytes"] if sha == TRAFFIC["kernel_sha256_16"] else None
+    for name in TRAFFIC_PARAMS:
+        h.update(f"{name}={sv.get_param(getattr(gb, name))};".encode())
+    return h.hexdigest()[:16]
+
+
+def _traffic(sv):
+    return TRAFFIC["bytes"] if TRAFFIC["key"] and traffic_key(sv) == TRAFFIC["key"] else None
 
 
 def _published_pi():
@@ -82,35 +96,79 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running.
+
+    One sampler can be made the process's shared one (share()): later samplers then
+    start no nvidia-smi of their own and summarise the shared sampler's samples that
+    arrived inside their own window.  Starting and stopping a sampler per workload
+    was seen to lift the served p99 that followed from 3 to 23 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    _shared = None
 
     def __init__(self, gpu_id: str):
         self.gpu_id = gpu_id
         self.proc = None
-        self.lines = []
+        self.thread = None
+        self.samples = []  # (arrival time, line)
+        self.proxy = None
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.samples.append((time.perf_counter(), line))
+
+    def share(self):
+        """Start this sampler and make it the shared one (until close())."""
+        self.__enter__()
+        ClockSampler._shared = self
+        return self
+
+    def close(self):
+        if ClockSampler._shared is self:
+            ClockSampler._shared = None
+        self.__exit__()
 
     def __enter__(self):
+        self.t0 = time.perf_counter()
+        if ClockSampler._shared is not None:
+            self.proxy = ClockSampler._shared
+            return self
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
         except OSError:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+        self.t1 = time.perf_counter()
+        if self.proxy is not None or self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            self.proc.wait()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    @property
+    def lines(self):
+        """Samples inside the window; for a window shorter than the sampling period, the
+        samples nearest to it (within 0.3 s on either side)."""
+        src = self.proxy.samples if self.proxy is not None else self.samples
+        t1 = self.t1 if self.t1 is not None else time.perf_counter()
+        inside = [l for t, l in src if self.t0 <= t <= t1]
+        return inside or [l for t, l in src if self.t0 - 0.3 <= t <= t1 + 0.3]
 
     def summary(self):
         sm, smax, reasons = [], [], set()
@@ -279,12 +337,13 @@ def run_gpu(args):
     peaks, peak_kind = _peaks()
     clocks = clk.summary()
     n_sms = props.multi_processor_count
-    clears = sv.crossing_work(lo, hi)          # the method's bit-clears (primes >= 23)
-    atomics = sv.crossing_work(lo, hi, 61)     # those the kernel makes as atomics (primes >= 61)
+    clears = sv.crossing_work(lo, hi)                       # the method's bit-clears (primes >= 23)
+    atomics = sv.crossing_work(lo, hi, _atomic_pmin(sv))    # those the kernel makes as atomics
     probes = _probe_rates(sv) if ws == 1 else None
     roof = _op_roofline(clears, ms_step * 1e-3, n_sms, peaks, peak_kind,
                         probes["smem_and_conflict_free_lanes_per_clk_sm"] if probes else None, atomics)
-    roof["traffic"] = _traffic() if args.hi is None and ws == 1 else None
+    roof["traffic"] = _traffic(sv) if args.hi is None and ws == 1 else None
+    roof["traffic_key"] = traffic_key(sv)
     line = None
     if rank == 0:
         line = {
@@ -357,6 +416,13 @@ def _op_roofline(clears, seconds, n_sms, peaks, peak_kind, probe=None, atomics=N
         if probe:
             out["frac_atomics_of_probe"] = atomics / seconds / (n_sms * probe * sm_max * 1e6)
     return out
+
+
+def _atomic_pmin(sv):
+    """The first prime the count kernel crosses with atomics: the ones below it come
+    from the pre-sieved patterns (SIEVE_PARAM_PRESIEVE 19, 59 or 71)."""
+    import paper_1205_4883_gb300 as gb
+    return {19: 23, 59: 61, 71: 73}[sv.get_param(gb.SIEVE_PARAM_PRESIEVE)]
 
 
 def _probe_rates(sv):
@@ -443,7 +509,7 @@ def batched_measure(steps=10, warmup=3, cpu=True, tuned=True):
     peaks, peak_kind = _peaks()
     n_sms = torch.cuda.get_device_properties(0).multi_processor_count
     clears = sum(sv.crossing_work(l, h) for l, h in zip(los, his))
-    atomics = sum(sv.crossing_work(l, h, 61) for l, h in zip(los, his))
+    atomics = sum(sv.crossing_work(l, h, _atomic_pmin(sv)) for l, h in zip(los, his))
     probe = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_CONFLICT_FREE)
     out = {"value": units / dt, "unit": METRIC, "ms_per_step": dt * 1e3, "steps": steps, "warmup": warmup,
            "config": {"workload": "batched: 4096 intervals, seed 1205, lo log-uniform [1e6, 1e14], "
@@ -458,7 +524,7 @@ def batched_measure(steps=10, warmup=3, cpu=True, tuned=True):
     if tuned:
         from paper_1205_4883_gb300 import autotune
         table = autotune.load_table()
-        if table.get("classes"):
+        if table:
             # the per-range parameters are planned once (host table lookup), then every
             # call is one graph launch with each range's class parameters
             pa = autotune.range_params_array(table, los, his)
@@ -473,12 +539,27 @@ def batched_measure(steps=10, warmup=3, cpu=True, tuned=True):
             tdt = (time.perf_counter() - t0) / steps
             out["tuned"] = {"value": units / tdt, "unit": METRIC, "ms_per_step": tdt * 1e3,
                             "vs_untuned": dt / tdt, "table": "paper_1205_4883_gb300/tuned.json",
-                            "classes": len(table["classes"])}
+                            "classes_overridden": len(table.get("classes", {})),
+                            "tuning": table.get("timing_ms")}
     sv.close()
     if cpu:
-        order = list(range(4096))
-        out["cpu_baseline"] = _cpu_intervals([(los[i], his[i], "count") for i in order])
+        out["cpu_baseline"] = batched_cpu_baseline()
     return out
+
+
+def batched_cpu_baseline():
+    """The oracle on the 4096 intervals (bounded sample, in the given order)."""
+    from paper_1205_4883_gb300.workloads import batch_intervals
+    los, his = batch_intervals(4096, seed=1205)
+    return _cpu_intervals([(a, b, "count") for a, b in zip(los, his)])
+
+
+def served_cpu_baseline(served):
+    """The oracle on the requests of the served stream the line's value comes from."""
+    from paper_1205_4883_gb300.workloads import served_stream
+    best = max(served["rates"], key=lambda r: r["integers_per_s"])
+    reqs = served_stream(rate=best["offered_req_s"], n=best["requests"], seed=1205)
+    return _cpu_intervals([(r.lo, r.hi, r.kind) for r in reqs])
 
 
 def run_batched(args):
@@ -579,7 +660,7 @@ def outputs_measure(lo, hi, name, with_count, steps=10, warmup=3, cpu=True):
     peaks, peak_kind = _peaks()
     n_sms = torch.cuda.get_device_properties(0).multi_processor_count
     clears = sv.crossing_work(lo, hi)
-    atomics = sv.crossing_work(lo, hi, 61)
+    atomics = sv.crossing_work(lo, hi, _atomic_pmin(sv))
     probe = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_CONFLICT_FREE)
     wbuf = torch.empty(2 << 30, dtype=torch.uint8, device="cuda")
     hbm_write = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_HBM_WRITE, wbuf)
@@ -623,15 +704,108 @@ def run_outputs(args, lo, hi, name, with_count):
     return 0
 
 
-def served_measure(rates, requests=0, cpu=True, **server_kw):
-    """A seeded Poisson stream (80% count, 20% list; lo log-uniform in [0, 1e12], width
-    log-uniform in [1e4, 1e9]) at each offered rate through the request server:
-    p50/p99 latency (submit to result on the host) and integers/s, against the plain
-    single-range sieve of the same number of integers at the stream's median start."""
+def _serve_stream(sv, reqs, rate, server_kw):
+    """Play one request stream against a server on sv (arrivals at their times, admission
+    retried while full), collect results through the completion queue and release them.
+    Returns the per-rate record."""
     import queue
     import threading
 
     import numpy as np
+    import torch
+    import paper_1205_4883_gb300 as gb
+    with gb.Server(sv, max_device_bytes=16 << 30, **server_kw) as srv:
+        tickets = queue.Queue()
+        lat, errors, kinds = [], [], {}
+
+        def collect():  # drains the completion queue, reads each result and releases it (frees slots)
+            expected, done = None, 0
+            deadline = time.perf_counter() + 900
+            while (expected is None or done < expected) and time.perf_counter() < deadline:
+                while True:
+                    try:
+                        t = tickets.get_nowait()
+                    except queue.Empty:
+                        break
+                    if t is None:
+                        expected = len(kinds)
+                for t in srv.wait_any(4096, timeout_us=2000):
+                    rc, res = srv.poll(t, timeout_us=0, copy_primes=False)
+                    if res["status"] != gb.SIEVE_OK:
+                        errors.append(res)
+                    else:
+                        lat.append((res["latency_us"], t, res["count"]))
+                    srv.release(t)
+                    done += 1
+            if expected is None or done < expected:
+                errors.append(f"{(expected or 0) - done} requests unfinished after 900 s")
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = time.perf_counter()
+        rejected = 0
+        for r in reqs:
+            now = time.perf_counter() - t0
+            if r.arrival_s > now:
+                time.sleep(r.arrival_s - now)
+            kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
+            rc, t = srv.submit(r.lo, r.hi, kind)
+            give_up = time.perf_counter() + 120
+            while rc == gb.SIEVE_EBUSY:  # admission is full: retry (bounded)
+                if time.perf_counter() > give_up:
+                    tickets.put(None)
+                    th.join()
+                    raise RuntimeError("served: a request was refused for 120 s")
+                rejected += 1
+                time.sleep(0.0005)
+                rc, t = srv.submit(r.lo, r.hi, kind)
+            kinds[t] = r.kind
+            tickets.put(t)
+        tickets.put(None)
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        if errors:
+            raise RuntimeError(f"served requests failed: {errors[:3]}")
+    ints = sum(r.hi - r.lo for r in reqs)
+    by_kind = {}
+    for kd in ("count", "list"):
+        xs = [x for x, t, _ in lat if kinds[t] == kd]
+        if xs:
+            by_kind[kd] = {"n": len(xs), "p50_ms": float(np.percentile(xs, 50)) / 1e3,
+                           "p99_ms": float(np.percentile(xs, 99)) / 1e3}
+    lat_all = [x for x, _, _ in lat]
+    list_bytes = 8 * sum(c for _, t, c in lat if kinds[t] == "list")  # uint64 results copied to the host
+    return {"offered_req_s": rate, "requests": len(reqs), "integers_per_s": ints / wall,
+            "p50_ms": float(np.percentile(lat_all, 50)) / 1e3, "p99_ms": float(np.percentile(lat_all, 99)) / 1e3,
+            "by_kind": by_kind, "wall_s": wall, "busy_retries": rejected, "ticks": st["ticks"],
+            "segments": st["segments"], "tick_gpu_ms": st["tick_gpu_ms"], "list_bytes_to_host": list_bytes}
+
+
+def _d2h_gbs():
+    """Pinned device-to-host copy bandwidth (GB/s), best of three 2 GiB copies."""
+    import torch
+    d = torch.empty(2 << 30, dtype=torch.uint8, device="cuda")
+    h = torch.empty(2 << 30, dtype=torch.uint8, pin_memory=True)
+    h.copy_(d)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(3):
+        t0 = time.perf_counter()
+        h.copy_(d)
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+    return (2 << 30) / best / 1e9
+
+
+def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000.0), **server_kw):
+    """A seeded Poisson stream (80% count, 20% list; lo log-uniform in [0, 1e12], width
+    log-uniform in [1e4, 1e9]) at each offered rate through the request server:
+    p50/p99 latency (submit to result on the host) and integers/s, against the plain
+    single-range sieve of the same number of integers at the stream's median start.  The
+    list results (uint64 primes) go to host memory, so the mixed stream is bound by the
+    device-to-host copy bandwidth: its roofline is that copy.  The same stream with count
+    requests only (the sieve side of the server) is reported beside it."""
     import torch
     import paper_1205_4883_gb300 as gb
     from paper_1205_4883_gb300.workloads import served_stream
@@ -642,86 +816,31 @@ def served_measure(rates, requests=0, cpu=True, **server_kw):
             n = requests or int(min(10000, max(300, rate)))
             reqs = served_stream(rate=rate, n=n, seed=1205)
             all_reqs.append(reqs)
-            with gb.Server(sv, max_device_bytes=16 << 30, **server_kw) as srv:
-                tickets = queue.Queue()
-                lat, errors = [], []
-
-                kinds = {}
-
-                def collect():  # drains the completion queue, reads each result and releases it (frees slots)
-                    expected, done = None, 0
-                    deadline = time.perf_counter() + 900
-                    while (expected is None or done < expected) and time.perf_counter() < deadline:
-                        while True:
-                            try:
-                                t = tickets.get_nowait()
-                            except queue.Empty:
-                                break
-                            if t is None:
-                                expected = len(kinds)
-                        for t in srv.wait_any(4096, timeout_us=2000):
-                            rc, res = srv.poll(t, timeout_us=0, copy_primes=False)
-                            if res["status"] != gb.SIEVE_OK:
-                                errors.append(res)
-                            else:
-                                lat.append((res["latency_us"], t))
-                            srv.release(t)
-                            done += 1
-                    if expected is None or done < expected:
-                        errors.append(f"{(expected or 0) - done} requests unfinished after 900 s")
-
-                th = threading.Thread(target=collect)
-                th.start()
-                t0 = time.perf_counter()
-                rejected = 0
-                for r in reqs:
-                    now = time.perf_counter() - t0
-                    if r.arrival_s > now:
-                        time.sleep(r.arrival_s - now)
-                    kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
-                    rc, t = srv.submit(r.lo, r.hi, kind)
-                    give_up = time.perf_counter() + 120
-                    while rc == gb.SIEVE_EBUSY:  # admission is full: retry (bounded)
-                        if time.perf_counter() > give_up:
-                            tickets.put(None)
-                            th.join()
-                            raise RuntimeError("served: a request was refused for 120 s")
-                        rejected += 1
-                        time.sleep(0.0005)
-                        rc, t = srv.submit(r.lo, r.hi, kind)
-                    kinds[t] = r.kind
-                    tickets.put(t)
-                tickets.put(None)
-                th.join()
-                wall = time.perf_counter() - t0
-                st = srv.stats()
-                if errors:
-                    raise RuntimeError(f"served requests failed: {errors[:3]}")
-            ints = sum(r.hi - r.lo for r in reqs)
-            lat_all = [x for x, _ in lat]
-            by_kind = {}
-            for kd in ("count", "list"):
-                xs = [x for x, t in lat if kinds[t] == kd]
-                if xs:
-                    by_kind[kd] = {"n": len(xs), "p50_ms": float(np.percentile(xs, 50)) / 1e3,
-                                   "p99_ms": float(np.percentile(xs, 99)) / 1e3}
-            results.append({"offered_req_s": rate, "requests": len(reqs), "integers_per_s": ints / wall,
-                            "p50_ms": float(np.percentile(lat_all, 50)) / 1e3,
-                            "p99_ms": float(np.percentile(lat_all, 99)) / 1e3, "by_kind": by_kind,
-                            "wall_s": wall, "busy_retries": rejected, "ticks": st["ticks"],
-                            "segments": st["segments"], "tick_gpu_ms": st["tick_gpu_ms"]})
+            results.append(_serve_stream(sv, reqs, rate, server_kw))
+        count_only = []
+        for rate in count_only_rates:
+            n = requests or int(min(10000, max(300, rate)))
+            count_only.append(_serve_stream(sv, served_stream(rate=rate, n=n, seed=1205, list_frac=0.0), rate,
+                                            server_kw))
     best_i = max(range(len(results)), key=lambda i: results[i]["integers_per_s"])
     best = results[best_i]
     reqs = all_reqs[best_i]
     units = sum(r.hi - r.lo for r in reqs)
     med = sorted(r.lo for r in reqs)[len(reqs) // 2]
     plain = _plain_same_integers(sv, med, units)
+    d2h = _d2h_gbs()
     peaks, peak_kind = _peaks()
     n_sms = torch.cuda.get_device_properties(0).multi_processor_count
     clears = sum(sv.crossing_work(r.lo, r.hi) for r in reqs)
-    atomics = sum(sv.crossing_work(r.lo, r.hi, 61) for r in reqs)
+    atomics = sum(sv.crossing_work(r.lo, r.hi, _atomic_pmin(sv)) for r in reqs)
     probe = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_CONFLICT_FREE)
     sv.close()
+    d2h_line = {"bound": "d2h", "op": "list results (uint64) copied to pinned host memory",
+                "achieved": best["list_bytes_to_host"] / best["wall_s"] / 1e9, "peak": d2h, "unit": "GB/s",
+                "frac": best["list_bytes_to_host"] / best["wall_s"] / 1e9 / d2h,
+                "peak_basis": "pinned device-to-host copy, 2 GiB, best of 3 (measured in this run)",
+                "bytes": best["list_bytes_to_host"]}
+    co_best = max(count_only, key=lambda r: r["integers_per_s"]) if count_only else None
     out = {"value": best["integers_per_s"], "unit": METRIC,
            "config": {"workload": "served: seeded Poisson stream, 80% count / 20% list, lo log-uniform "
                                   "[0, 1e12], w log-uniform [1e4, 1e9]", "seed": 1205,
@@ -730,10 +849,16 @@ def served_measure(rates, requests=0, cpu=True, **server_kw):
            "rates": results,
            "vs_plain": best["integers_per_s"] / plain["value"],
            "plain_single_range": plain,
-           "roofline": _op_roofline(clears, best["wall_s"], n_sms, peaks, peak_kind, probe, atomics),
+           "roofline": d2h_line,
+           "roofline_sieve": _op_roofline(clears, best["wall_s"], n_sms, peaks, peak_kind, probe, atomics),
            "clocks": clk.summary()}
+    if co_best is not None:
+        out["count_only"] = {"value": co_best["integers_per_s"], "unit": METRIC,
+                             "vs_plain": co_best["integers_per_s"] / plain["value"],
+                             "workload": "the same stream with list_frac 0 (every request a count)",
+                             "rates": count_only}
     if cpu:
-        out["cpu_baseline"] = _cpu_intervals([(r.lo, r.hi, r.kind) for r in reqs])
+        out["cpu_baseline"] = served_cpu_baseline(out)
     return out
 
 
@@ -793,22 +918,48 @@ def main():
         return run_outputs(args, 0, 10**7, "[0, 10^7): count, odd-only bitmap and u32 prime list", True)
     if args.workload == "peaks":
         return run_peaks(args)
-    line = run_gpu(args)
-    ws, rank, _ = _dist()
+    ws, rank, local = _dist()
+    shared = None
+    if ws == 1:  # one nvidia-smi for the whole run; every workload reads its own window
+        import torch
+        torch.cuda.set_device(0)
+        shared = ClockSampler(_gpu_id(0)).share()
+    try:
+        sub = {}
+        if ws == 1 and not args.no_sub:
+            # the metric's "batched/served vs plain": all on the same GPU, same process.  All GPU
+            # measurements come before the CPU-oracle baselines (a multi-second oracle run on
+            # every host core, with its large allocations, was seen to lift the served p99 that
+            # followed it from 3 to 17 ms); the served stream, the workload most sensitive to
+            # what ran before it in the process, comes first.
+            rates = [float(r) for r in args.default_rates.split(",")]
+            sub["served"] = served_measure(rates, cpu=False)
+            sub["batched"] = batched_measure(args.steps, args.warmup, cpu=False)
+            sub["pi1e7"] = outputs_measure(0, 10**7, "[0, 10^7): count, odd-only bitmap and u32 prime list",
+                                           True, args.steps, args.warmup, cpu=False)
+            sub["range2p32"] = outputs_measure(0, 1 << 32, "[0, 2^32): odd-only bitmap and u32 prime list",
+                                               False, args.steps, args.warmup, cpu=False)
+        line = run_gpu(args)
+        if line is not None:
+            line.update(sub)
+        _finish_default_line(args, line, ws, rank)
+    finally:
+        if shared is not None:
+            shared.close()
+    return 0
+
+
+def _finish_default_line(args, line, ws, rank):
     if rank == 0 and line is not None:
         if ws == 1 and not args.no_sub:
-            # the metric's "batched/served vs plain": both on the same GPU, same process
-            line["batched"] = batched_measure(args.steps, args.warmup, cpu=not args.no_cpu_baseline)
-            line["served"] = served_measure([float(r) for r in args.default_rates.split(",")],
-                                            cpu=not args.no_cpu_baseline)
-            line["pi1e7"] = outputs_measure(0, 10**7, "[0, 10^7): count, odd-only bitmap and u32 prime list",
-                                            True, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
-            line["range2p32"] = outputs_measure(0, 1 << 32, "[0, 2^32): odd-only bitmap and u32 prime list",
-                                                False, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+            if not args.no_cpu_baseline:
+                line["batched"]["cpu_baseline"] = batched_cpu_baseline()
+                line["served"]["cpu_baseline"] = served_cpu_baseline(line["served"])
+                line["pi1e7"]["cpu_baseline"] = _cpu_outputs(0, 10**7, True)
+                line["range2p32"]["cpu_baseline"] = _cpu_outputs(0, 1 << 32, False)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample()
         print(json.dumps(line))
-    return 0
 
 
 if __name__ == "__main__":

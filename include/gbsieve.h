@@ -225,6 +225,8 @@ typedef struct {
                                   slot, so the next tick's CTAs fill the SMs the previous tick's
                                   last segments leave idle */
     uint32_t reserved;
+    uint64_t host_arena_bytes; /* pinned host memory that list results are copied into by DMA
+                                  (0: 1 GiB); results that do not fit go through a bounce buffer */
 } sieve_server_cfg;
 
 typedef struct {
@@ -318,8 +320,9 @@ void sieve_server_destroy(sieve_server *srv);
                                         sieve does when a bounded wait in a kernel runs out */
 #define SIEVE_PARAM_PRESIEVE      15 /* mod-30 kernels: largest prime whose multiples come from
                                         pre-sieved patterns ANDed into each segment instead of being
-                                        crossed: 19 (one pattern, 7..19) or 59 (default: three further
-                                        patterns, 23..31, 37..43 and 47..59); results are the same */
+                                        crossed: 19 (one pattern, 7..19), 59 (three further patterns,
+                                        23..31, 37..43 and 47..59) or 71 (default: a fourth, 61..71);
+                                        results are the same */
 #define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
                                        primes, carried across the segments of a work item; used
                                        when they fit and enough segments resume one (half of a

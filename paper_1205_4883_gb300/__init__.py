@@ -63,7 +63,8 @@ class sieve_info(ctypes.Structure):
 
 class sieve_server_cfg(ctypes.Structure):
     _fields_ = [("max_requests", ctypes.c_uint32), ("tick_segments", ctypes.c_uint32),
-                ("max_device_bytes", _u64), ("serial_ticks", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("max_device_bytes", _u64), ("serial_ticks", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("host_arena_bytes", _u64)]
 
 
 class sieve_req(ctypes.Structure):
@@ -383,8 +384,9 @@ def sieve_stream(ctx: int) -> int:
 
 
 def sieve_server_create(ctx: int, max_requests: int = 0, tick_segments: int = 0, max_device_bytes: int = 0,
-                        serial_ticks: bool = False) -> int:
-    cfg = sieve_server_cfg(max_requests, tick_segments, max_device_bytes, 1 if serial_ticks else 0, 0)
+                        serial_ticks: bool = False, host_arena_bytes: int = 0) -> int:
+    cfg = sieve_server_cfg(max_requests, tick_segments, max_device_bytes, 1 if serial_ticks else 0, 0,
+                           host_arena_bytes)
     h = _vp()
     rc = load_library().sieve_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h))
     _check(ctx, rc)
@@ -449,9 +451,10 @@ class Server:
     """A continuous-batching request server on a Sieve context."""
 
     def __init__(self, sieve: "Sieve", max_requests: int = 0, tick_segments: int = 0, max_device_bytes: int = 0,
-                 serial_ticks: bool = False):
+                 serial_ticks: bool = False, host_arena_bytes: int = 0):
         self.sieve = sieve  # keeps the context alive
-        self.srv = sieve_server_create(sieve.ctx, max_requests, tick_segments, max_device_bytes, serial_ticks)
+        self.srv = sieve_server_create(sieve.ctx, max_requests, tick_segments, max_device_bytes, serial_ticks,
+                                       host_arena_bytes)
 
     def submit(self, lo, hi, kind=SIEVE_REQ_COUNT):
         return sieve_server_submit(self.srv, lo, hi, kind)

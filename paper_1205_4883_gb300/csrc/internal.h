@@ -34,15 +34,19 @@ constexpr uint32_t kFirstCrossingPrime = 8u;
 constexpr uint32_t kXTilePeriod0 = 20677u;  // 23 * 29 * 31
 constexpr uint32_t kXTilePeriod1 = 65231u;  // 37 * 41 * 43
 constexpr uint32_t kXTilePeriod2 = 146969u; // 47 * 53 * 59
+constexpr uint32_t kXTilePeriod3 = 290177u; // 61 * 67 * 71 (a fourth pattern, SIEVE_PARAM_PRESIEVE = 71)
 constexpr uint64_t tile_copy_bytes(uint32_t period) {
     return ((uint64_t)period + kMaxSegmentBytes + 32 + 15) & ~15ull;
 }
 constexpr uint64_t kXTileStride0 = tile_copy_bytes(kXTilePeriod0);
 constexpr uint64_t kXTileStride1 = tile_copy_bytes(kXTilePeriod1);
 constexpr uint64_t kXTileStride2 = tile_copy_bytes(kXTilePeriod2);
+constexpr uint64_t kXTileStride3 = tile_copy_bytes(kXTilePeriod3);
 // Index of the first base prime >= 61: the first one crossed when the
 // further patterns are applied.
 constexpr uint32_t kFirstCrossingPrimeX = 17u;
+// Index of the first base prime >= 73: the first one crossed with the fourth pattern.
+constexpr uint32_t kFirstCrossingPrimeX4 = 20u;
 
 // One range of a launch.  Segment s of the range covers wheel bytes
 // [Bbase + s S, Bbase + (s + 1) S); Bbase is chosen so that 30 Bbase + 1 is
@@ -87,6 +91,7 @@ struct SieveLaunch {
     uint32_t mr_end;                     // index of the first base prime >= 2^16
     uint64_t mr_square;                  // that prime squared: survivors below it need no test
     const uint32_t *mr_list;             // ranges on the Miller-Rabin path
+    const uint32_t *mr_words;            // n_mr + 1 prefix sums of their words (the filter's flat index)
     uint32_t n_mr;
     uint32_t *cursors;                   // null, or grid x cursor_stride wheel cursors of the large primes
     uint32_t cursor_stride;              // large primes per CTA (from mid_end)
@@ -96,6 +101,7 @@ struct SieveLaunch {
     uint32_t small_first;                // first prime of the small tier: kFirstCrossingPrime, or
                                          // kFirstCrossingPrimeX with the further patterns
     const uint8_t *xtile0, *xtile1, *xtile2;  // null, or copy 0 of each further pattern (mod-30 kernels)
+    const uint8_t *xtile3;                    // null, or copy 0 of the fourth pattern (61 * 67 * 71)
 };
 // Bytes reserved for the SieveLaunch at the head of a launch block; the
 // RangeDescs follow it.

@@ -310,6 +310,19 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
     }
     for (uint32_t q = 0; q < n_mr; ++q)
         if (scratch_at[q] != ~(size_t)0) rd[lb.h_mr()[q]].bitmap = ctx->mr.d + scratch_at[q];
+    // prefix sums of the words the Miller-Rabin filter scans (raw wheel words in count
+    // mode, odd-only words in bitmap mode), one thread per word
+    {
+        uint32_t *pw = lb.h_mrw();
+        uint64_t acc = 0;
+        for (uint32_t q = 0; q < n_mr; ++q) {
+            pw[q] = (uint32_t)acc;
+            const RangeDesc &r = rd[lb.h_mr()[q]];
+            acc += mode == kModeCount ? (uint64_t)((((int64_t)r.hi - 30 * r.Bbase + 29) / 30 + 31) & ~31ll) / 4
+                                      : r.bitmap_words;
+        }
+        pw[n_mr] = (uint32_t)acc;
+    }
     SieveLaunch &L = *reinterpret_cast<SieveLaunch *>(lb.h_block);
     std::memset(&L, 0, sizeof L);
     L.ranges = lb.d_ranges();
@@ -322,11 +335,15 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
     L.magic = ctx->d_magic;
     L.tile = ctx->d_tile;
     L.tile_stride = ctx->tile_stride;
-    if (prm.presieve == 59) {
+    if (prm.presieve >= 59) {
         L.xtile0 = ctx->d_tile + ctx->tile_stride * kTileCopies;
         L.xtile1 = L.xtile0 + kXTileStride0 * kTileCopies;
         L.xtile2 = L.xtile1 + kXTileStride1 * kTileCopies;
         L.small_first = kFirstCrossingPrimeX;
+        if (prm.presieve == 71) {
+            L.xtile3 = L.xtile2 + kXTileStride2 * kTileCopies;
+            L.small_first = kFirstCrossingPrimeX4;
+        }
     } else {
         L.small_first = kFirstCrossingPrime;
     }
@@ -337,6 +354,7 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
     L.mr_end = mr_end;
     L.mr_square = mr_square;
     L.mr_list = lb.d_mr();
+    L.mr_words = lb.d_mrw();
     L.n_mr = n_mr;
     L.bucket_first = bfirst;
     if (buckets) {
@@ -379,8 +397,10 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
 int enqueue_launch(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
                    int grid, int mr_grid, size_t n_list) {
     CK(cudaMemcpyAsync(lb.d_block, lb.h_block, kLaunchHeader + m * sizeof(RangeDesc), cudaMemcpyHostToDevice, stream));
-    if (n_list)
+    if (n_list) {
         CK(cudaMemcpyAsync(lb.d_mr(), lb.h_mr(), n_list * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(lb.d_mrw(), lb.h_mrw(), (n_list + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+    }
     CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
     const SieveLaunch *d = reinterpret_cast<const SieveLaunch *>(lb.d_block);
     const uint32_t smem = reinterpret_cast<const SieveLaunch *>(lb.h_block)->seg_bytes;  // the largest segment
@@ -397,7 +417,7 @@ int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mo
     const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
     const uint32_t n_mr = reinterpret_cast<const SieveLaunch *>(lb.h_block)->n_mr;
     return enqueue_launch(ctx, stream, prm, mode, lb, m, (int)std::min<uint64_t>(grid, items),
-                          (int)std::min<uint64_t>(n_mr, 4ull * ctx->num_sms), n_mr);
+                          n_mr ? 8 * ctx->num_sms : 0, n_mr);
 }
 
 // Segment size of the mod-210 count path: the configured segment rounded down
@@ -758,7 +778,7 @@ int batch_graph(sieve_ctx *ctx, int mode, size_t m, size_t m210, const RangeOver
         const int grid = ctx->num_sms * prm.ctas_per_sm;
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        if (m) rc = enqueue_launch(ctx, ctx->capture_stream, prm, mode, ctx->lb, m, grid, 4 * ctx->num_sms, m);
+        if (m) rc = enqueue_launch(ctx, ctx->capture_stream, prm, mode, ctx->lb, m, grid, 8 * ctx->num_sms, m);
         if (!rc && m210) rc = enqueue_launch210(ctx, ctx->capture_stream, prm, ctx->lb210, m210, grid);
         cudaError_t e1 = cudaSuccess;
         if (m)
@@ -952,19 +972,23 @@ int sieve_create(sieve_ctx **out, uint64_t hi_max, int device, void *cuda_stream
     // segment; the primes 7..19, then the further patterns 23..31, 37..43, 47..59
     const uint64_t len = tile_copy_bytes(kTilePeriod);
     ctx->tile_stride = len;
-    int rc = dev_alloc(ctx, &ctx->d_tile, (len + kXTileStride0 + kXTileStride1 + kXTileStride2) * kTileCopies);
+    int rc = dev_alloc(ctx, &ctx->d_tile,
+                       (len + kXTileStride0 + kXTileStride1 + kXTileStride2 + kXTileStride3) * kTileCopies);
     if (rc) return bail(rc);
     {
         static const uint32_t pa[] = {7, 11, 13, 17, 19}, pb[] = {23, 29, 31}, pc[] = {37, 41, 43},
                               pd[] = {47, 53, 59};
+        static const uint32_t pe[] = {61, 67, 71};
         uint8_t *x0 = ctx->d_tile + len * kTileCopies, *x1 = x0 + kXTileStride0 * kTileCopies,
-                *x2 = x1 + kXTileStride1 * kTileCopies;
+                *x2 = x1 + kXTileStride1 * kTileCopies, *x3 = x2 + kXTileStride2 * kTileCopies;
         e = launch_build_tile(ctx->d_tile, len, (uint32_t)len, kTilePeriod, pa, 5, ctx->stream);
         if (e == cudaSuccess) e = launch_build_tile(x0, kXTileStride0, (uint32_t)kXTileStride0, kXTilePeriod0, pb, 3,
                                                     ctx->stream);
         if (e == cudaSuccess) e = launch_build_tile(x1, kXTileStride1, (uint32_t)kXTileStride1, kXTilePeriod1, pc, 3,
                                                     ctx->stream);
         if (e == cudaSuccess) e = launch_build_tile(x2, kXTileStride2, (uint32_t)kXTileStride2, kXTilePeriod2, pd, 3,
+                                                    ctx->stream);
+        if (e == cudaSuccess) e = launch_build_tile(x3, kXTileStride3, (uint32_t)kXTileStride3, kXTilePeriod3, pe, 3,
                                                     ctx->stream);
         if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "build tile"));
     }
@@ -1196,7 +1220,7 @@ int sieve_set_param(sieve_ctx *ctx, int param, int64_t v) {
             p.fault_wait = (int)v;
             break;
         case SIEVE_PARAM_PRESIEVE:
-            if (v != 19 && v != 59) return fail(ctx, SIEVE_EINVAL, "pre-sieve limit (19 or 59)");
+            if (v != 19 && v != 59 && v != 71) return fail(ctx, SIEVE_EINVAL, "pre-sieve limit (19, 59 or 71)");
             p.presieve = (uint32_t)v;
             break;
         case SIEVE_PARAM_SMALL_LIMIT_210:

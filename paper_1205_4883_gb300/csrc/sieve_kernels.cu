@@ -167,58 +167,6 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
-// ---------------------------------------------------------------- Miller-Rabin
-
-// Montgomery product a b R^-1 mod n (R = 2^64) for odd n < 2^62 and a, b < n,
-// with nprime = -n^-1 mod 2^64: t = a b, m = (t mod R) nprime, and
-// (t + m n) / R < 2 n, less n if needed.  The low word of t + m n is 0, so
-// the carry out of it is 1 exactly when t's low word is not 0.
-__device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t n, uint64_t nprime) {
-    const uint64_t lo = a * b, hi = __umul64hi(a, b);
-    const uint64_t m = lo * nprime;
-    const uint64_t r = hi + __umul64hi(m, n) + (lo != 0);
-    return r >= n ? r - n : r;
-}
-
-// Deterministic Miller-Rabin for odd n < 2^62 with no prime factor below 37:
-// the first twelve primes as bases decide every n < 3.18e23 (Sorenson and
-// Webster, "Strong pseudoprimes to twelve prime bases", Math. Comp. 86, 2017).
-// a^d mod n is the paper's exponentiation by squaring (Section 3.2, Algorithm
-// 2), carried out on Montgomery residues.
-__device__ __noinline__ bool mr_is_prime(uint64_t n) {
-    uint64_t inv = n;  // n^-1 mod 2^64 by Newton steps (n is its own inverse mod 8)
-#pragma unroll
-    for (int i = 0; i < 5; ++i) inv *= 2 - n * inv;
-    const uint64_t nprime = 0 - inv;
-    const uint64_t one = (0 - n) % n;  // R mod n: Montgomery form of 1
-    uint64_t r2 = one;                 // R^2 mod n by 64 doublings
-    for (int i = 0; i < 64; ++i) {
-        r2 <<= 1;
-        if (r2 >= n) r2 -= n;
-    }
-    const uint64_t minus_one = n - one;
-    uint64_t d = n - 1;
-    const int s = __ffsll((long long)d) - 1;
-    d >>= s;
-    const uint32_t bases[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
-    for (int b = 0; b < 12; ++b) {
-        uint64_t y = mont_mul(bases[b], r2, n, nprime);  // a R mod n
-        uint64_t x = one;
-        for (uint64_t e = d; e; e >>= 1) {  // Algorithm 2: x = a^d mod n
-            if (e & 1) x = mont_mul(x, y, n, nprime);
-            y = mont_mul(y, y, n, nprime);
-        }
-        if (x == one || x == minus_one) continue;
-        bool witness = true;
-        for (int r = 1; r < s && witness; ++r) {
-            x = mont_mul(x, x, n, nprime);
-            if (x == minus_one) witness = false;
-        }
-        if (witness) return false;
-    }
-    return true;
-}
-
 // Number of base primes among primes[0, n) with p^2 < E (a prefix, since the
 // primes ascend), found by one warp with 32-way probing.  Every lane of the
 // warp must call it; all lanes return the result.
@@ -426,7 +374,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
     __shared__ uint32_t s_cnt[kMaxChunkSegments];  // bucket fill counts, one per segment of the chunk
     __shared__ __align__(8) uint64_t s_tile_bar;    // completes the pattern copy of each segment
     __shared__ uint32_t s_tile_fail;                // a wait for it hit kWaitLimit: the CTA stops
-    __shared__ uint32_t s_xph[3];                   // B0 mod the periods of the further patterns
+    __shared__ uint32_t s_xph[4];                   // B0 mod the periods of the further patterns
     __shared__ uint32_t s_midG;                     // medium groups dealt by cost (0: round-robin)
     __shared__ uint32_t s_midW[kMidGroups + 1];     // their cumulative costs
     uint32_t tile_phase = 0;
@@ -571,6 +519,8 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                         s_xph[0] = (uint32_t)(x0 < 0 ? x0 + kXTilePeriod0 : x0);
                         s_xph[1] = (uint32_t)(x1 < 0 ? x1 + kXTilePeriod1 : x1);
                         s_xph[2] = (uint32_t)(x2 < 0 ? x2 + kXTilePeriod2 : x2);
+                        const int64_t x3 = B0 % (int64_t)kXTilePeriod3;
+                        s_xph[3] = (uint32_t)(x3 < 0 ? x3 + kXTilePeriod3 : x3);
                     }
                 }
             }
@@ -611,7 +561,7 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             //     fused into the popcount epilogue instead (step 4), which reads every
             //     word anyway -- except in the segment holding wheel bytes 0 and 1,
             //     whose fix-up (step 3) must come after the patterns.
-            const bool fuse_x = MODE == kModeCount && P.xtile0 && !(B0 <= 1 && B0 + (int64_t)L > 0);
+            const bool fuse_x = MODE == kModeCount && P.xtile0 && !(B0 <= 2 && B0 + (int64_t)L > 0);
             if (P.xtile0 && !fuse_x) {
                 const uint4 *x0 = reinterpret_cast<const uint4 *>(P.xtile0 + (s_xph[0] & 15u) * kXTileStride0 +
                                                                   (s_xph[0] & ~15u));
@@ -619,6 +569,9 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                                                                   (s_xph[1] & ~15u));
                 const uint4 *x2 = reinterpret_cast<const uint4 *>(P.xtile2 + (s_xph[2] & 15u) * kXTileStride2 +
                                                                   (s_xph[2] & ~15u));
+                const uint4 *x3 = P.xtile3 ? reinterpret_cast<const uint4 *>(P.xtile3 + (s_xph[3] & 15u) * kXTileStride3 +
+                                                                             (s_xph[3] & ~15u))
+                                           : nullptr;
                 for (uint32_t q = tid; q < L / 16; q += blockDim.x) {
                     const uint4 a = __ldg(x0 + q), b = __ldg(x1 + q), c = __ldg(x2 + q);
                     uint4 v = smem4[q];
@@ -626,6 +579,13 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                     v.y &= a.y & b.y & c.y;
                     v.z &= a.z & b.z & c.z;
                     v.w &= a.w & b.w & c.w;
+                    if (x3) {
+                        const uint4 d = __ldg(x3 + q);
+                        v.x &= d.x;
+                        v.y &= d.y;
+                        v.z &= d.z;
+                        v.w &= d.w;
+                    }
                     smem4[q] = v;
                 }
                 __syncthreads();
@@ -774,10 +734,12 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
 
             // 3. wheel bytes 0 and 1 (integers 1..59): 1 and 49 are not prime, the
             //    others are, though the patterns clear 7..19 and 23..59
-            if (B0 <= 1 && B0 + (int64_t)L > 0) {  // the same for the whole CTA
+            if (B0 <= 2 && B0 + (int64_t)L > 0) {  // the same for the whole CTA
                 if (tid == 0) {
                     if (B0 <= 0) seg[-B0] = 0xFE;
-                    if (1 - B0 < (int64_t)L) seg[1 - B0] = 0xDF;
+                    if (B0 <= 1 && 1 - B0 < (int64_t)L) seg[1 - B0] = 0xDF;
+                    // wheel byte 2 (61..89): 77 is the one composite; the fourth pattern clears 61, 67, 71
+                    if (P.xtile3 && 2 - B0 < (int64_t)L) seg[2 - B0] = 0xEF;
                 }
                 __syncthreads();
             }
@@ -798,7 +760,16 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                 }
                 if (!raw && lo_rel <= 0 && hi_rel >= 30 * (int64_t)L) {
                     // the whole segment lies in [lo, hi): no masks, 16-byte loads
-                    if (fuse_x) {
+                    if (fuse_x && P.xtile3) {
+                        const uint4 *x3 = reinterpret_cast<const uint4 *>(P.xtile3 + (s_xph[3] & 15u) * kXTileStride3 +
+                                                                          (s_xph[3] & ~15u));
+                        for (uint32_t q = tid; q < L / 16; q += blockDim.x) {
+                            const uint4 a = __ldg(x0 + q), b = __ldg(x1 + q), c = __ldg(x2 + q), d = __ldg(x3 + q);
+                            const uint4 v = smem4[q];
+                            cnt += __popc(v.x & a.x & b.x & c.x & d.x) + __popc(v.y & a.y & b.y & c.y & d.y) +
+                                   __popc(v.z & a.z & b.z & c.z & d.z) + __popc(v.w & a.w & b.w & c.w & d.w);
+                        }
+                    } else if (fuse_x) {
                         for (uint32_t q = tid; q < L / 16; q += blockDim.x) {
                             const uint4 a = __ldg(x0 + q), b = __ldg(x1 + q), c = __ldg(x2 + q);
                             const uint4 v = smem4[q];
@@ -815,9 +786,14 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
                     const uint32_t *y0 = reinterpret_cast<const uint32_t *>(x0),
                                    *y1 = reinterpret_cast<const uint32_t *>(x1),
                                    *y2 = reinterpret_cast<const uint32_t *>(x2);
+                    const uint32_t *y3 = fuse_x && P.xtile3
+                                             ? reinterpret_cast<const uint32_t *>(P.xtile3 + (s_xph[3] & 15u) * kXTileStride3 +
+                                                                                  (s_xph[3] & ~15u))
+                                             : nullptr;
                     for (uint32_t w = tid; w < L / 4; w += blockDim.x) {
                         uint32_t v = seg32[w];
                         if (fuse_x) v &= __ldg(y0 + w) & __ldg(y1 + w) & __ldg(y2 + w);
+                        if (y3) v &= __ldg(y3 + w);
                         if (raw) raw[w] = v;
                         const int64_t wb = 120 * (int64_t)w;
                         if (wb < lo_rel || wb + 120 > hi_rel) v &= range_mask(wb, lo_rel, hi_rel);
@@ -878,57 +854,6 @@ __global__ void __launch_bounds__(1024, 1) k_sieve(const SieveLaunch *__restrict
             if (tid == 0) atomicOr(P.overflow, 2u);
             break;
         }
-    }
-}
-
-// ---------------------------------------------------------------- Miller-Rabin filter
-
-// Survivors of the sieve by the primes below 2^16 in the ranges on the
-// Miller-Rabin path (P->mr_list[0 .. P->n_mr)), one CTA per range: every
-// survivor in [lo, hi) at or above P->mr_square is tested; a composite is
-// subtracted from its range's count and, in bitmap mode, loses its bit.
-// Count mode reads the raw wheel words k_sieve left (ODD = false); bitmap mode
-// the odd-only words of the output (ODD = true).  Each such range is one
-// segment long.
-template <bool ODD>
-__global__ void __launch_bounds__(256) k_mr_filter(const SieveLaunch *__restrict__ P) {
-    __shared__ unsigned long long s_red[8];
-    const uint32_t n_mr = P->n_mr;
-    for (uint32_t q = blockIdx.x; q < n_mr; q += gridDim.x) {
-        const uint32_t r = P->mr_list[q];
-        const RangeDesc &rd = P->ranges[r];
-        uint32_t *words = rd.bitmap;
-        unsigned long long composites = 0;
-        if (words) {
-            const uint64_t o0 = rd.lo | 1;
-            const int64_t base_int = 30 * rd.Bbase;
-            const uint64_t nwords = ODD ? rd.bitmap_words
-                                        : (uint64_t)((((int64_t)rd.hi - base_int + 29) / 30 + 31) & ~31ll) / 4;
-            for (uint64_t w = threadIdx.x; w < nwords; w += blockDim.x) {
-                uint32_t v = words[w], keep = v;
-                while (v) {
-                    const int b = __ffs(v) - 1;
-                    v &= v - 1;
-                    const int64_t n = ODD ? (int64_t)(o0 + 64 * w + 2 * (uint64_t)b)
-                                          : base_int + 120 * (int64_t)w + 30 * (b >> 3) + (int64_t)c_res[b & 7];
-                    if (n < (int64_t)rd.lo || n >= (int64_t)rd.hi || (uint64_t)n < P->mr_square) continue;
-                    if (!mr_is_prime((uint64_t)n)) {
-                        keep &= ~(1u << b);
-                        ++composites;
-                    }
-                }
-                if (ODD && keep != words[w]) words[w] = keep;
-            }
-        }
-        composites = warp_sum(composites);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = composites;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long c = 0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) c += s_red[i];
-            if (c) atomicAdd(P->counts + r, 0ull - c);
-        }
-        __syncthreads();
     }
 }
 
@@ -1003,14 +928,6 @@ cudaError_t launch_sieve(int mode, const SieveLaunch *d_launch, int grid, int th
         k_sieve<kModeCount><<<grid, threads, seg_bytes, stream>>>(d_launch);
     else
         k_sieve<kModeBitmap><<<grid, threads, seg_bytes, stream>>>(d_launch);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mr_filter(int mode, const SieveLaunch *d_launch, int grid, cudaStream_t stream) {
-    if (mode == kModeCount)
-        k_mr_filter<false><<<grid, 256, 0, stream>>>(d_launch);
-    else
-        k_mr_filter<true><<<grid, 256, 0, stream>>>(d_launch);
     return cudaGetLastError();
 }
 

@@ -183,7 +183,7 @@ void complete(sieve_server *srv, Req *r, int status) {
 }
 
 constexpr size_t kBounceWords = 2u << 20;  // 16 MiB of uint64 per finisher
-constexpr size_t kHostArenaBytes = 1ull << 30;  // pinned host memory for list results
+constexpr size_t kHostArenaBytes = 1ull << 30;  // pinned host memory for list results (default)
 
 // Called without the lock: compaction of a finished list request into its
 // device list, then one DMA copy into the pinned host arena -- or, when the
@@ -402,8 +402,13 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
     };
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking);
+    // Finishers on the highest-priority streams: a sieve CTA holds a whole SM (all
+    // its registers), so compaction kernels run only where one has left; with
+    // priority their CTAs take a freed SM before the next tick's waiting CTAs.
+    int prio_low = 0, prio_high = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     for (Finisher &f : srv->fin)
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&f.stream, cudaStreamNonBlocking, prio_high);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "server streams"));
     v->stream = srv->stream;
     // the Miller-Rabin path keeps raw words in one scratch of the view, which two
@@ -432,10 +437,11 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
     }
     // list results go here by DMA; without it (pinning refused) they take the bounce path
     unsigned char *ha = nullptr;
-    if (cudaMallocHost(&ha, kHostArenaBytes) == cudaSuccess) {
+    const size_t hbytes = srv->cfg.host_arena_bytes ? srv->cfg.host_arena_bytes : kHostArenaBytes;
+    if (cudaMallocHost(&ha, hbytes) == cudaSuccess) {
         srv->host_arena.base = ha;
-        srv->host_arena.size = kHostArenaBytes;
-        srv->host_arena.free_blocks[0] = kHostArenaBytes;
+        srv->host_arena.size = hbytes;
+        srv->host_arena.free_blocks[0] = hbytes;
     } else {
         cudaGetLastError();  // clear the refused allocation's error
     }

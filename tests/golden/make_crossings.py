@@ -5,8 +5,9 @@ The paper prints no such values.  Each line is the number of pairs (p, m),
 p prime >= pmin with p^2 < hi, m >= p, gcd(m, wheel) = 1, lo <= p m < hi:
 the bit-clears of Section 3.1's marking of multiples on a wheel of that
 modulus.  pmin = 23 is the work of the mod-30 sieve after the pattern of
-7..19 (every clear, however the kernel makes it); pmin = 61 the clears left
-after the further patterns of 23..59; wheel 210 the mod-210 count path.
+7..19 (every clear, however the kernel makes it); pmin = 61 and 73 the clears
+left after the further patterns of 23..59 and 23..71; wheel 210 the mod-210
+count path.
 
   python tests/golden/make_crossings.py
 """
@@ -19,7 +20,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import oracle  # noqa: E402
 
 RANGES = [
-    (0, 10**12, 23, 30), (0, 10**12, 61, 30), (0, 10**12, 23, 210),
+    (0, 10**12, 23, 30), (0, 10**12, 61, 30), (0, 10**12, 73, 30), (0, 10**12, 23, 210),
     (0, 1 << 32, 23, 30), (0, 1 << 32, 61, 30),
     (0, 10**7, 23, 30), (0, 10**7, 61, 30),
     (10**14, 10**14 + 10**10, 23, 30), (10**14, 10**14 + 10**10, 61, 30),

@@ -162,7 +162,7 @@ def test_tier_limits_do_not_change_results(mid):
             assert np.array_equal(words.cpu().numpy().view(np.uint32), oracle.bitmap(lo, hi)), (lo, hi)
 
 
-@pytest.mark.parametrize("presieve", [19, 59])
+@pytest.mark.parametrize("presieve", [19, 59, 71])
 @pytest.mark.parametrize("small", [23, 61, 512])
 def test_presieve_patterns_do_not_change_results(presieve, small):
     # primes 23..59 crossed one by one (19) or ANDed in as three patterns (59), with the
@@ -173,6 +173,7 @@ def test_presieve_patterns_do_not_change_results(presieve, small):
         s.set_param(gb.SIEVE_PARAM_SMALL_LIMIT, small)
         assert s.get_param(gb.SIEVE_PARAM_PRESIEVE) == presieve
         for lo, hi in [(0, 10**7), (0, 60), (1, 61), (30, 90), (31, 32), (47, 48), (49, 50), (53, 60),
+                       (60, 90), (61, 62), (67, 68), (71, 72), (73, 74), (77, 78), (0, 100), (59, 200),
                        (5, 40_000), (10**12 - 10**6, 10**12 + 10**6), (9 * 10**12, 9 * 10**12 + 2 * 10**7)]:
             assert s.count(lo, hi) == oracle.count(lo, hi), (lo, hi)
             words, _ = s.bitmap(lo, hi)
@@ -478,3 +479,26 @@ def test_roofline_probes_report_plausible_rates(sv):
     assert 1000 < gbs < 20000
     with pytest.raises(gb.SieveError):
         gb.sieve_probe(sv.ctx, 99)
+
+
+def test_compaction_into_unaligned_and_offset_outputs(sv):
+    # list outputs at every 4-byte (u32) and 8-byte (u64) offset from a 16-byte boundary:
+    # the emit's 16-byte stores apply only when the output is aligned, and neighbouring
+    # entries outside the list are never written
+    lo, hi = 10**9 - 12_345, 10**9 + 3_000_000
+    want = oracle.primes(lo, hi)
+    n = len(want)
+    for off in range(4):
+        buf = torch.full((n + 8,), -1, dtype=torch.int32, device="cuda")
+        got_n, rc = gb.sieve_list(sv.ctx, lo, hi, buf[off:], n)
+        assert rc == gb.SIEVE_OK and got_n == n
+        h = buf.cpu().numpy()
+        assert np.array_equal(h[off:off + n].view(np.uint32).astype(np.uint64), want), off
+        assert (h[:off] == -1).all() and (h[off + n:] == -1).all(), off
+    for off in range(2):
+        buf = torch.full((n + 4,), -1, dtype=torch.int64, device="cuda")
+        got_n, rc = gb.sieve_list64(sv.ctx, lo, hi, buf[off:], n)
+        assert rc == gb.SIEVE_OK and got_n == n
+        h = buf.cpu().numpy()
+        assert np.array_equal(h[off:off + n].view(np.uint64), want), off
+        assert (h[:off] == -1).all() and (h[off + n:] == -1).all(), off
