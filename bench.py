@@ -38,7 +38,7 @@ METRIC = "integers sieved/s"
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass, full launch);
 # reported only while the kernel source AND the launch parameters are the ones
 # it was measured with (both are part of the key).
-TRAFFIC = {"key": None, "bytes": None}
+TRAFFIC = {"key": "e40fc78c7c432258", "bytes": 317.28e6 + 1920.27e6}
 WORKLOAD = "pi(10^12): count primes in [0, 10^12), one range, count-only, mod-30 wheel + pre-sieved patterns"
 # the launch parameters that shape the kernel's memory traffic
 TRAFFIC_PARAMS = ("SIEVE_PARAM_SEGMENT_BYTES", "SIEVE_PARAM_THREADS", "SIEVE_PARAM_SMALL_LIMIT",
@@ -704,69 +704,68 @@ def run_outputs(args, lo, hi, name, with_count):
     return 0
 
 
-def _serve_stream(sv, reqs, rate, server_kw):
-    """Play one request stream against a server on sv (arrivals at their times, admission
+def _serve_stream(srv, reqs, rate):
+    """Play one request stream against the server srv (arrivals at their times, admission
     retried while full), collect results through the completion queue and release them.
-    Returns the per-rate record."""
+    Returns the per-rate record (counters as differences over the stream)."""
     import queue
     import threading
 
     import numpy as np
-    import torch
     import paper_1205_4883_gb300 as gb
-    with gb.Server(sv, max_device_bytes=16 << 30, **server_kw) as srv:
-        tickets = queue.Queue()
-        lat, errors, kinds = [], [], {}
+    st0 = srv.stats()
+    tickets = queue.Queue()
+    lat, errors, kinds = [], [], {}
 
-        def collect():  # drains the completion queue, reads each result and releases it (frees slots)
-            expected, done = None, 0
-            deadline = time.perf_counter() + 900
-            while (expected is None or done < expected) and time.perf_counter() < deadline:
-                while True:
-                    try:
-                        t = tickets.get_nowait()
-                    except queue.Empty:
-                        break
-                    if t is None:
-                        expected = len(kinds)
-                for t in srv.wait_any(4096, timeout_us=2000):
-                    rc, res = srv.poll(t, timeout_us=0, copy_primes=False)
-                    if res["status"] != gb.SIEVE_OK:
-                        errors.append(res)
-                    else:
-                        lat.append((res["latency_us"], t, res["count"]))
-                    srv.release(t)
-                    done += 1
-            if expected is None or done < expected:
-                errors.append(f"{(expected or 0) - done} requests unfinished after 900 s")
+    def collect():  # drains the completion queue, reads each result and releases it (frees slots)
+        expected, done = None, 0
+        deadline = time.perf_counter() + 900
+        while (expected is None or done < expected) and time.perf_counter() < deadline:
+            while True:
+                try:
+                    t = tickets.get_nowait()
+                except queue.Empty:
+                    break
+                if t is None:
+                    expected = len(kinds)
+            for t in srv.wait_any(4096, timeout_us=2000):
+                rc, res = srv.poll(t, timeout_us=0, copy_primes=False)
+                if res["status"] != gb.SIEVE_OK:
+                    errors.append(res)
+                else:
+                    lat.append((res["latency_us"], t, res["count"]))
+                srv.release(t)
+                done += 1
+        if expected is None or done < expected:
+            errors.append(f"{(expected or 0) - done} requests unfinished after 900 s")
 
-        th = threading.Thread(target=collect)
-        th.start()
-        t0 = time.perf_counter()
-        rejected = 0
-        for r in reqs:
-            now = time.perf_counter() - t0
-            if r.arrival_s > now:
-                time.sleep(r.arrival_s - now)
-            kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    rejected = 0
+    for r in reqs:
+        now = time.perf_counter() - t0
+        if r.arrival_s > now:
+            time.sleep(r.arrival_s - now)
+        kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
+        rc, t = srv.submit(r.lo, r.hi, kind)
+        give_up = time.perf_counter() + 120
+        while rc == gb.SIEVE_EBUSY:  # admission is full: retry (bounded)
+            if time.perf_counter() > give_up:
+                tickets.put(None)
+                th.join()
+                raise RuntimeError("served: a request was refused for 120 s")
+            rejected += 1
+            time.sleep(0.0005)
             rc, t = srv.submit(r.lo, r.hi, kind)
-            give_up = time.perf_counter() + 120
-            while rc == gb.SIEVE_EBUSY:  # admission is full: retry (bounded)
-                if time.perf_counter() > give_up:
-                    tickets.put(None)
-                    th.join()
-                    raise RuntimeError("served: a request was refused for 120 s")
-                rejected += 1
-                time.sleep(0.0005)
-                rc, t = srv.submit(r.lo, r.hi, kind)
-            kinds[t] = r.kind
-            tickets.put(t)
-        tickets.put(None)
-        th.join()
-        wall = time.perf_counter() - t0
-        st = srv.stats()
-        if errors:
-            raise RuntimeError(f"served requests failed: {errors[:3]}")
+        kinds[t] = r.kind
+        tickets.put(t)
+    tickets.put(None)
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    if errors:
+        raise RuntimeError(f"served requests failed: {errors[:3]}")
     ints = sum(r.hi - r.lo for r in reqs)
     by_kind = {}
     for kd in ("count", "list"):
@@ -778,8 +777,9 @@ def _serve_stream(sv, reqs, rate, server_kw):
     list_bytes = 8 * sum(c for _, t, c in lat if kinds[t] == "list")  # uint64 results copied to the host
     return {"offered_req_s": rate, "requests": len(reqs), "integers_per_s": ints / wall,
             "p50_ms": float(np.percentile(lat_all, 50)) / 1e3, "p99_ms": float(np.percentile(lat_all, 99)) / 1e3,
-            "by_kind": by_kind, "wall_s": wall, "busy_retries": rejected, "ticks": st["ticks"],
-            "segments": st["segments"], "tick_gpu_ms": st["tick_gpu_ms"], "list_bytes_to_host": list_bytes}
+            "by_kind": by_kind, "wall_s": wall, "busy_retries": rejected, "ticks": st["ticks"] - st0["ticks"],
+            "segments": st["segments"] - st0["segments"], "tick_gpu_ms": st["tick_gpu_ms"] - st0["tick_gpu_ms"],
+            "list_bytes_to_host": list_bytes}
 
 
 def _d2h_gbs():
@@ -811,17 +811,18 @@ def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000
     from paper_1205_4883_gb300.workloads import served_stream
     sv = gb.Sieve(10**12 + 10**9 + 1)
     results, all_reqs = [], []
-    with ClockSampler(_gpu_id(torch.cuda.current_device())) as clk:
+    # one server for every stream (its arenas pinned and allocated once)
+    with ClockSampler(_gpu_id(torch.cuda.current_device())) as clk, \
+            gb.Server(sv, max_device_bytes=16 << 30, **server_kw) as srv:
         for rate in rates:
             n = requests or int(min(10000, max(300, rate)))
             reqs = served_stream(rate=rate, n=n, seed=1205)
             all_reqs.append(reqs)
-            results.append(_serve_stream(sv, reqs, rate, server_kw))
+            results.append(_serve_stream(srv, reqs, rate))
         count_only = []
         for rate in count_only_rates:
             n = requests or int(min(10000, max(300, rate)))
-            count_only.append(_serve_stream(sv, served_stream(rate=rate, n=n, seed=1205, list_frac=0.0), rate,
-                                            server_kw))
+            count_only.append(_serve_stream(srv, served_stream(rate=rate, n=n, seed=1205, list_frac=0.0), rate))
     best_i = max(range(len(results)), key=lambda i: results[i]["integers_per_s"])
     best = results[best_i]
     reqs = all_reqs[best_i]

@@ -289,9 +289,9 @@ void sieve_server_destroy(sieve_server *srv);
 /* Tunable launch parameters (see sieve_set_param / sieve_get_param). */
 #define SIEVE_PARAM_SEGMENT_BYTES 1 /* shared-memory segment, bytes; multiple of 32 */
 #define SIEVE_PARAM_THREADS       2 /* threads per CTA: 256, 512 or 1024 */
-#define SIEVE_PARAM_SMALL_LIMIT   3 /* primes below this are crossed warp-cooperatively (default 448) */
+#define SIEVE_PARAM_SMALL_LIMIT   3 /* primes below this are crossed warp-cooperatively (default 304) */
 #define SIEVE_PARAM_CTAS_PER_SM   4 /* persistent CTAs per SM */
-#define SIEVE_PARAM_CHUNK_SEGMENTS 5 /* consecutive segments per work item (1..64) */
+#define SIEVE_PARAM_CHUNK_SEGMENTS 5 /* consecutive segments per work item (1..64; default 32) */
 #define SIEVE_PARAM_BUCKET_LIMIT  6 /* primes >= this go through bucket lists; 0 = segment bytes;
                                        default 2^62 (off: direct crossing measured faster) */
 #define SIEVE_PARAM_MR_PERCENT    8 /* a range of width w < this % of the base primes above 2^16

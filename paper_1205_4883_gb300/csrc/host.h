@@ -17,10 +17,11 @@ namespace gbs {
 struct Params {
     uint32_t seg_bytes = kMaxSegmentBytes;
     int threads = 1024;
-    uint32_t small_limit = 448;   // measured best on pi(10^12) among 384..576 (64..1792 before the dealing by cost)
+    uint32_t small_limit = 304;   // measured best on pi(10^12) with the patterns up to 71: swept 208..544 in
+                                  // steps of 16 (448 was best with the patterns up to 59)
     uint32_t mid_limit = 0;       // primes below this use per-phase sub-progressions; 0: segment bytes / 3
     int ctas_per_sm = 1;
-    uint32_t chunk_segs = 16;
+    uint32_t chunk_segs = 32;      // segments per work item (24, 32: within 0.05 ms; 64 and 16 slower)
     uint64_t bucket_limit = 1ull << 62;  // primes >= this use the bucket lists; 0: the segment size
     uint32_t cursor_mb = 1024;           // budget for per-CTA large-prime cursors (0: recompute every segment)
     uint32_t mr_percent = 0;             // Miller-Rabin path when width < this % of the skipped primes (0: off)
