@@ -320,8 +320,8 @@ void sieve_server_destroy(sieve_server *srv);
                                         sieve does when a bounded wait in a kernel runs out */
 #define SIEVE_PARAM_PRESIEVE      15 /* mod-30 kernels: largest prime whose multiples come from
                                         pre-sieved patterns ANDed into each segment instead of being
-                                        crossed: 19 (one pattern, 7..19), 59 (three further patterns,
-                                        23..31, 37..43 and 47..59) or 71 (default: a fourth, 61..71);
+                                        crossed: 19 (one pattern, 7..19), 59 (default: three further
+                                        patterns, 23..31, 37..43 and 47..59) or 71 (a fourth, 61..71);
                                         results are the same */
 #define SIEVE_PARAM_CURSOR_MB     7 /* device memory (MiB) for per-CTA wheel cursors of the large
                                        primes, carried across the segments of a work item; used

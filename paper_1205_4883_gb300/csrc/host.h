@@ -30,8 +30,9 @@ struct Params {
     uint32_t mid_limit210 = 0;           // mod-210: primes below this use per-class sub-progressions; 0: words / 6
     int batch_order = 0;                 // batches: 0 as given, 1 heaviest first, 2 heaviest/lightest alternating
     int fault_wait = 0;                  // test hook: synchronous launches report a device-wait failure
-    uint32_t presieve = 71;              // mod-30: largest prime applied as a pattern (19, 59 or 71); 71
-                                         // measured best on pi(10^12): 147.7 ms against 149.1 ms for 59
+    uint32_t presieve = 59;              // mod-30: largest prime applied as a pattern (19, 59 or 71); with
+                                         // the small limit re-tuned, 71 is 0.15 % faster on pi(10^12) but its
+                                         // 8 MB of pattern copies evict the cursors: 7x the DRAM traffic
 };
 
 // Everything one sieve launch reads and writes besides the resident state:
