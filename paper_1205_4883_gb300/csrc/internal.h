@@ -168,7 +168,7 @@ cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint
 // With total != null, writes only if *total + base_index <= cap (else nothing).
 cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets,
                         uint64_t ntiles, uint64_t o0, uint32_t base_index, void *out,
-                        int out64, int grid, cudaStream_t stream,
+                        int out64, int num_sms, cudaStream_t stream,
                         const unsigned long long *total = nullptr, uint64_t cap = 0);
 cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream);
 // out[0] = 2 if *total + 1 <= cap.

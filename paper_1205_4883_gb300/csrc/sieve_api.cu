@@ -555,8 +555,8 @@ int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const 
         CK(launch_tile_scan(cs.counts, cs.offsets, ntiles, cs.d_total, stream));
         if (out_dev) {
             if (two) CK(launch_put_two_if_fits(out_dev, out64, cs.d_total, cap, stream));
-            CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, lo | 1, two, out_dev, out64, grid, stream,
-                           cs.d_total, cap));
+            CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, lo | 1, two, out_dev, out64, ctx->num_sms,
+                           stream, cs.d_total, cap));
         }
         CK(cudaMemcpyAsync(cs.h_total, cs.d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));

@@ -9,6 +9,8 @@
 // bytes); in pass 3 it holds eight consecutive words (k_emit).
 #include "internal.h"
 
+#include <atomic>
+
 namespace gbs {
 namespace {
 
@@ -105,27 +107,47 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t *tile_counts,
 // directly).
 constexpr uint32_t kEmitStage = 1024;
 
+// The primes of one lane's eight words, written downwards from p (exclusive):
+// words 7 .. 0, in each word its set bits from the highest, so the values land
+// in ascending order.  v is the integer of bit 0 of word 0.
+template <typename T, typename V>
+__device__ __forceinline__ void emit_lane_desc(const uint32_t (&w)[8], V v, T *p) {
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        const V vk = v + (V)(64u * (uint32_t)k);
+        for (uint32_t x = w[k]; x;) {
+            const uint32_t b = 31u - (uint32_t)__clz(x);
+            *--p = (T)(vk + (V)(2u * b));
+            x ^= 1u << b;
+        }
+    }
+}
+
 // Pass 3.  Warp w of a CTA takes words [256 w, 256 w + 256) of the tile, lane l
 // the eight consecutive words 8 l .. 8 l + 7 of those (two 16-byte loads per
 // lane, so a load instruction reads 512 contiguous bytes).  One warp scan of the
 // lanes' popcounts ranks every prime of the warp's words; each lane writes its
-// primes, in order, into the warp's stage in shared memory, and the warp copies
-// the stage out as one contiguous run.  With total != null the list is written
-// only if it fits: *total (from k_tile_scan) + base_index <= cap; otherwise the
+// primes into the warp's stage in shared memory, and the warp copies the stage
+// out as one contiguous run.  The warps' prime counts go through a two-slot
+// table (by tile parity), so one barrier per tile suffices: a warp can be at
+// most one tile ahead of another.  With total != null the list is written only
+// if it fits: *total (from k_tile_scan) + base_index <= cap; otherwise the
 // kernel writes nothing, so the host can launch it before it has read the total.
 template <typename T>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ bitmap, uint64_t nwords,
                                               const uint64_t *__restrict__ tile_offsets, uint64_t ntiles,
                                               uint64_t o0, uint32_t base_index, T *__restrict__ out,
                                               const unsigned long long *total, uint64_t cap) {
-    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_warp[2][8];
     extern __shared__ __align__(16) unsigned char s_dyn[];  // 8 stages of kEmitStage entries
     if (total && *total + base_index > cap) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool vec = (reinterpret_cast<uintptr_t>(bitmap) & 15u) == 0;
     T *const stage = reinterpret_cast<T *>(s_dyn) + (size_t)warp * kEmitStage;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint32_t par = 0;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, par ^= 1u) {
         const uint64_t w0 = t * kCompactTileWords + 256ull * warp + 8ull * lane;  // this lane's first word
+        const uint64_t toff = tile_offsets[t];
         uint32_t w[8];
         if (vec && w0 + 8 <= nwords) {
             const uint4 a = __ldg(reinterpret_cast<const uint4 *>(bitmap + w0));
@@ -141,29 +163,31 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ bitma
         for (int k = 0; k < 8; ++k) c += __popc(w[k]);
         const uint32_t incl = warp_inclusive_scan_u32(c, lane);
         const uint32_t n = __shfl_sync(0xffffffffu, incl, 31);  // primes in the warp's 256 words
-        if (lane == 0) s_warp[warp] = n;
+        if (lane == 0) s_warp[par][warp] = n;
         __syncthreads();
-        uint64_t first = base_index + tile_offsets[t];  // rank of the warp's first prime
-        for (int i = 0; i < warp; ++i) first += s_warp[i];
-        uint64_t v = o0 + 64ull * w0;  // integer of bit 0 of the lane's first word
+        uint64_t first = base_index + toff;  // rank of the warp's first prime
+        for (int i = 0; i < warp; ++i) first += s_warp[par][i];
+        const uint64_t v = o0 + 64ull * w0;  // integer of bit 0 of the lane's first word
         if (n <= kEmitStage) {
-            uint32_t j = incl - c;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                for (uint32_t x = w[k]; x; x &= x - 1) stage[j++] = (T)(v + 2ull * (uint32_t)(__ffs(x) - 1));
-                v += 64;
-            }
+            if (sizeof(T) == 4)
+                emit_lane_desc(w, (uint32_t)v, stage + incl);  // a 32-bit list holds values below 2^32
+            else
+                emit_lane_desc(w, v, stage + incl);
             __syncwarp();
-            for (uint32_t i = lane; i < n; i += 32) out[first + i] = stage[i];
-        } else {
-            uint64_t pos = first + incl - c;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                for (uint32_t x = w[k]; x; x &= x - 1) out[pos++] = (T)(v + 2ull * (uint32_t)(__ffs(x) - 1));
-                v += 64;
+            T *const o = out + first;
+            uint32_t i = lane;
+            for (; i + 96 < n; i += 128) {
+                const T a0 = stage[i], a1 = stage[i + 32], a2 = stage[i + 64], a3 = stage[i + 96];
+                o[i] = a0; o[i + 32] = a1; o[i + 64] = a2; o[i + 96] = a3;
             }
+            for (; i < n; i += 32) o[i] = stage[i];
+            __syncwarp();  // the stage is refilled by the next tile
+        } else {
+            if (sizeof(T) == 4)
+                emit_lane_desc(w, (uint32_t)v, out + first + incl);
+            else
+                emit_lane_desc(w, v, out + first + incl);
         }
-        __syncthreads();  // s_warp and the stages are reused by the next tile
     }
 }
 
@@ -183,15 +207,40 @@ cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint
     return cudaGetLastError();
 }
 
+namespace {
+// CTAs of k_emit<T> resident per SM with its stage (the grid is that many per SM:
+// one wave, no tail of CTAs that start after the first ones have finished).  The
+// shared-memory attribute is set on every call (it belongs to the current device);
+// the occupancy is the same on every device of the one supported architecture.
+template <typename T>
+cudaError_t emit_ctas_per_sm(int *per_sm) {
+    static std::atomic<int> cached{0};
+    const int smem = 8 * kEmitStage * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_emit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int n = cached.load(std::memory_order_relaxed);
+    if (n <= 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_emit<T>, 256, smem);
+        if (e != cudaSuccess) return e;
+        if (n <= 0) n = 1;
+        cached.store(n, std::memory_order_relaxed);
+    }
+    *per_sm = n;
+    return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets, uint64_t ntiles,
-                        uint64_t o0, uint32_t base_index, void *out, int out64, int grid, cudaStream_t stream,
+                        uint64_t o0, uint32_t base_index, void *out, int out64, int num_sms, cudaStream_t stream,
                         const unsigned long long *total, uint64_t cap) {
     if (ntiles == 0) return cudaSuccess;
-    const unsigned g = (unsigned)(ntiles < (uint64_t)grid ? ntiles : (uint64_t)grid);
+    int per_sm = 0;
+    cudaError_t e = out64 ? emit_ctas_per_sm<uint64_t>(&per_sm) : emit_ctas_per_sm<uint32_t>(&per_sm);
+    if (e != cudaSuccess) return e;
+    const uint64_t grid = (uint64_t)num_sms * per_sm;
+    const unsigned g = (unsigned)(ntiles < grid ? ntiles : grid);
     if (out64) {
         const int smem = 8 * kEmitStage * sizeof(uint64_t);  // 64 KiB: above the default 48 KiB
-        cudaError_t e = cudaFuncSetAttribute(k_emit<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
         k_emit<uint64_t><<<g, 256, smem, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
                                                    static_cast<uint64_t *>(out), total, cap);
     } else {

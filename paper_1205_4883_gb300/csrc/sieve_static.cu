@@ -95,7 +95,7 @@ extern "C" int sieve_compact_static(const uint32_t *bitmap_dev, uint64_t lo, uin
         if (*n > cap) return SIEVE_ETRUNC;
         if (*n && !out_dev) return SIEVE_EINVAL;
         if (two && launch_put_two(out_dev, 0, stream) != cudaSuccess) return SIEVE_ECUDA;
-        if (launch_emit(bitmap_dev, nwords, tile_offsets, ntiles, o0, two, out_dev, 0, sms * 8, stream) !=
+        if (launch_emit(bitmap_dev, nwords, tile_offsets, ntiles, o0, two, out_dev, 0, sms, stream) !=
             cudaSuccess)
             return SIEVE_ECUDA;
         return cudaStreamSynchronize(stream) == cudaSuccess ? SIEVE_OK : SIEVE_ECUDA;
