@@ -606,17 +606,18 @@ def _cpu_outputs(lo, hi, with_count, budget_s=12.0):
 
 
 def outputs_measure(lo, hi, name, with_count, steps=10, warmup=3, cpu=True):
-    """One range's outputs through the C ABI into preallocated device buffers: (optionally the
-    count,) the odd-only bitmap (sieve_bitmap) and the prime list compacted from it
-    (sieve_compact, u32).  Per stage: CUDA-event time on the context's stream.  The bitmap
-    stage is the sieve kernel (bit-clears against the shared-memory op peak); the list stage
-    reads the bitmap twice and writes the list (HBM).  e2e adds the copy of the list to pinned
-    host memory."""
+    """One range's outputs through the C ABI into preallocated device buffers, as a stream
+    pipeline: the odd-only bitmap with its prime count (sieve_bitmap_dev), then the u32 prime
+    list compacted from it with its length (sieve_compact_dev), both asynchronous, so nothing
+    waits on the host inside a step.  Per stage: CUDA-event time on the context's stream.  The
+    bitmap stage is the sieve kernel (bit-clears against the shared-memory op peak); the list
+    stage reads the bitmap twice and writes the list (HBM).  e2e adds the copy of the list and
+    the two counts to pinned host memory and the synchronisation that waits for them."""
     import torch
     import paper_1205_4883_gb300 as gb
     torch.cuda.set_device(0)
     sv = gb.Sieve(hi)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.current_stream()  # the context runs on it
     nw = gb.sieve_bitmap_words(lo, hi)
     n = sv.count(lo, hi)
     published = _published_pi()
@@ -624,18 +625,17 @@ def outputs_measure(lo, hi, name, with_count, steps=10, warmup=3, cpu=True):
         raise RuntimeError(f"count of [0, {hi}) is {n}, the published pi({hi}) is {published[hi]}")
     bm = torch.empty(nw, dtype=torch.int32, device="cuda")
     lst = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
     host = torch.empty(max(n, 1), dtype=torch.int32, pin_memory=True)
+    host_cnt = torch.zeros(2, dtype=torch.int64, pin_memory=True)
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device="cuda")
 
     def stages(evs):
-        if with_count:
-            sv.count(lo, hi)
         evs[0].record(stream)
-        c = gb.sieve_bitmap(sv.ctx, lo, hi, bm)
+        gb.sieve_bitmap_dev(sv.ctx, lo, hi, bm, cnt[0:1])
         evs[1].record(stream)
-        k, rc = gb.sieve_compact(sv.ctx, bm, lo, hi, lst)
+        gb.sieve_compact_dev(sv.ctx, bm, lo, hi, lst, cnt[1:2])
         evs[2].record(stream)
-        return c, k
 
     for _ in range(warmup):
         stages([torch.cuda.Event(enable_timing=True) for _ in range(3)])
@@ -644,19 +644,23 @@ def outputs_measure(lo, hi, name, with_count, steps=10, warmup=3, cpu=True):
     with ClockSampler(_gpu_id(torch.cuda.current_device())) as clk:
         for k in range(steps):
             flush.zero_()
-            c, got = stages(evs[k])
+            stages(evs[k])
         torch.cuda.synchronize()
-    assert c == n and got == n
+    if cnt.tolist() != [n, n]:
+        raise RuntimeError(f"device counts {cnt.tolist()}, expected {n}")
     t_bm = sum(e[0].elapsed_time(e[1]) for e in evs) / steps
     t_ls = sum(e[1].elapsed_time(e[2]) for e in evs) / steps
-    # end to end: count (if asked), bitmap, list, and the list copied to pinned host memory
+    # end to end: bitmap, list, and the list and both counts copied to pinned host memory
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
         stages([torch.cuda.Event(enable_timing=True) for _ in range(3)])
         host.copy_(lst, non_blocking=True)
+        host_cnt.copy_(cnt, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / steps
+    if host_cnt.tolist() != [n, n] or (lo == 0 and hi > 2 and int(host[0]) != 2):
+        raise RuntimeError("end-to-end results differ from the count")
     peaks, peak_kind = _peaks()
     n_sms = torch.cuda.get_device_properties(0).multi_processor_count
     clears = sv.crossing_work(lo, hi)
@@ -669,7 +673,7 @@ def outputs_measure(lo, hi, name, with_count, steps=10, warmup=3, cpu=True):
     hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
     bm_line = _op_roofline(clears, t_bm * 1e-3, n_sms, peaks, peak_kind, probe, atomics)
     bm_line.update({"kernel": "k_sieve<1>", "traffic": None, "bitmap_bytes_written": 4 * nw})
-    ls_line = {"bound": "hbm", "kernel": "k_tile_popc + k_tile_scan + k_emit (sieve_compact)",
+    ls_line = {"bound": "hbm", "kernel": "k_tile_popc + k_tile_scan + k_emit (sieve_compact_dev)",
                "achieved": list_bytes / (t_ls * 1e-3) / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
                "frac": list_bytes / (t_ls * 1e-3) / hbm, "traffic": None, "bytes_per_call": list_bytes,
                "peak_basis": f"{peak_kind} hbm_gbs (copy, read + write)",
@@ -685,7 +689,10 @@ def outputs_measure(lo, hi, name, with_count, steps=10, warmup=3, cpu=True):
            "roofline": dominant, "roofline_list": ls_line, "roofline_bitmap": bm_line,
            "clocks": clk.summary(),
            "e2e": {"value": (hi - lo) / e2e_s, "unit": METRIC, "h2d_bytes_per_step": 72,
-                   "d2h_bytes_per_step": 4 * n + 8}}
+                   "d2h_bytes_per_step": 4 * n + 16},
+           # k_sieve<1>, k_finalize_count; k_tile_popc, k_tile_scan, (k_put_two_if_fits), k_emit,
+           # k_store_count
+           "launches_per_step": 6 + (1 if lo <= 2 < hi else 0)}
     sv.close()
     del bm, lst, host, flush
     if cpu:
@@ -698,7 +705,7 @@ def run_outputs(args, lo, hi, name, with_count):
     line = {"metric": METRIC, "value": out["value"], "unit": METRIC, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": out["config"],
-            "gpu_launches": args.steps * 5}
+            "gpu_launches": args.steps * out["launches_per_step"]}
     line.update({k: v for k, v in out.items() if k not in line})
     print(json.dumps(line))
     return 0

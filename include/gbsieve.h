@@ -78,7 +78,9 @@ int sieve_count(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count);
 /*
  * As sieve_count, but the count is written to the device integer
  * *count_dev and the call is ASYNCHRONOUS: it returns after enqueueing the
- * work on the context's stream.  *count_dev is overwritten.
+ * work on the context's stream.  *count_dev is overwritten (UINT64_MAX if a
+ * bucket list overflowed or a device-side wait gave up).  Calls may follow
+ * one another without a synchronisation.
  */
 int sieve_count_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_dev);
 
@@ -119,6 +121,28 @@ int sieve_list64(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out_dev,
  */
 int sieve_compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo,
                   uint64_t hi, uint32_t *out_dev, size_t cap, uint64_t *n);
+
+/*
+ * Asynchronous forms of sieve_bitmap and sieve_compact for stream pipelines
+ * (bitmap, then list, then whatever consumes it, with no host round trip).
+ * Arguments, layouts and argument errors are those of the synchronous calls,
+ * except that the count goes to a device integer and the call returns after
+ * enqueueing its work on the context's stream.  Buffers must stay valid until
+ * the stream has run the work.  Calls may follow one another without a
+ * synchronisation (a call first waits, on the host, until the previous call's
+ * launch parameters have been copied to the device).
+ *
+ * sieve_bitmap_dev: *count_dev (required) = the number of primes in [lo, hi),
+ *   or UINT64_MAX if a bucket list overflowed or a device-side wait gave up;
+ *   the bitmap is then not valid (the synchronous call retries instead).
+ * sieve_compact_dev: *n_dev = the number of primes in [lo, hi).  The list is
+ *   written only if it fits (*n_dev <= cap); otherwise nothing is written and
+ *   the caller sees *n_dev > cap after synchronising.  Requires hi <= 2^32.
+ */
+int sieve_bitmap_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev,
+                     size_t out_words, uint64_t *count_dev);
+int sieve_compact_dev(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo,
+                      uint64_t hi, uint32_t *out_dev, size_t cap, uint64_t *n_dev);
 
 /*
  * Batched counting: m ranges [lo[i], hi[i]) (host arrays) sieved by one

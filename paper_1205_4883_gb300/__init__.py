@@ -102,6 +102,8 @@ _SIGS = {
     "sieve_list": (_int, [_vp, _u64, _u64, _vp, _sz, _pu64]),
     "sieve_list64": (_int, [_vp, _u64, _u64, _vp, _sz, _pu64]),
     "sieve_compact": (_int, [_vp, _vp, _u64, _u64, _vp, _sz, _pu64]),
+    "sieve_bitmap_dev": (_int, [_vp, _u64, _u64, _vp, _sz, _vp]),
+    "sieve_compact_dev": (_int, [_vp, _vp, _u64, _u64, _vp, _sz, _vp]),
     "sieve_batch_count": (_int, [_vp, _pu64, _pu64, _sz, _pu64, ctypes.POINTER(_vp)]),
     "sieve_batch_count_params": (_int, [_vp, _pu64, _pu64, _sz, ctypes.POINTER(sieve_range_params), _pu64,
                                         ctypes.POINTER(_vp)]),
@@ -247,6 +249,22 @@ def sieve_compact(ctx: int, bitmap, lo: int, hi: int, out, cap: Optional[int] = 
     rc = load_library().sieve_compact(ctx, _ptr(bitmap), lo, hi, _ptr(out), cap, ctypes.byref(n))
     _check(ctx, rc, allow=(SIEVE_ETRUNC,))
     return n.value, rc
+
+
+def sieve_bitmap_dev(ctx: int, lo: int, hi: int, out, count_dev, out_words: Optional[int] = None) -> None:
+    """Asynchronous sieve_bitmap: the count goes to the device integer `count_dev`
+    (a one-element CUDA int64 tensor or a device address); nothing waits for the stream."""
+    if out_words is None:
+        out_words = out.numel() * out.element_size() // 4 if out is not None and not isinstance(out, int) else 0
+    _check(ctx, load_library().sieve_bitmap_dev(ctx, lo, hi, _ptr(out), out_words, _ptr(count_dev)))
+
+
+def sieve_compact_dev(ctx: int, bitmap, lo: int, hi: int, out, n_dev, cap: Optional[int] = None) -> None:
+    """Asynchronous sieve_compact: the prime count goes to the device integer `n_dev`; the
+    list is written only if it fits in `cap` (read n_dev after synchronising)."""
+    if cap is None:
+        cap = out.numel() * out.element_size() // 4 if out is not None and not isinstance(out, int) else 0
+    _check(ctx, load_library().sieve_compact_dev(ctx, _ptr(bitmap), lo, hi, _ptr(out), cap, _ptr(n_dev)))
 
 
 def sieve_compact_static(bitmap, lo: int, hi: int, out, cap: Optional[int] = None, stream: Optional[int] = None):

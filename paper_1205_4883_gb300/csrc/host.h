@@ -44,6 +44,10 @@ struct LaunchBuffers {
     unsigned long long *d_acc = nullptr;
     unsigned long long *h_acc = nullptr;  // pinned, [0..m] = counts, overflow
     size_t cap = 0;                        // ranges
+    // recorded on the stream after the block's host-to-device copies: an
+    // asynchronous call may return before they run, so the next writer of
+    // h_block waits for it (block_wait)
+    cudaEvent_t consumed = nullptr;
     RangeDesc *h_ranges() const { return reinterpret_cast<RangeDesc *>(h_block + kLaunchHeader); }
     RangeDesc *d_ranges() const { return reinterpret_cast<RangeDesc *>(d_block + kLaunchHeader); }
     // after the ranges: the indices of the ranges on the Miller-Rabin path, then the
@@ -162,6 +166,7 @@ RangeDesc plan_range(const sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t se
                      uint32_t *bitmap);
 int alloc_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb, size_t m);
 void free_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb);
+int block_wait(sieve_ctx *ctx, LaunchBuffers &lb);  // until lb.h_block may be rewritten
 int alloc_compact_scratch(sieve_ctx *ctx, CompactScratch &cs, size_t tiles);
 void free_compact_scratch(sieve_ctx *ctx, CompactScratch &cs);
 

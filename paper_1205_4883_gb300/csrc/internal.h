@@ -165,6 +165,8 @@ cudaError_t launch_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *
                              uint64_t ntiles, int grid, cudaStream_t stream);
 cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint64_t ntiles,
                              unsigned long long *total, cudaStream_t stream);
+// *n = (*total, or 0 if total is null) + add: the device-side count of the asynchronous compaction.
+cudaError_t launch_store_count(const unsigned long long *total, uint32_t add, uint64_t *n, cudaStream_t stream);
 // With total != null, writes only if *total + base_index <= cap (else nothing).
 cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets,
                         uint64_t ntiles, uint64_t o0, uint32_t base_index, void *out,

@@ -136,6 +136,7 @@ int alloc_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb, size_t m) {
     if (rc) return rc;
     CK(cudaMallocHost(&lb.h_block, block));
     CK(cudaMallocHost(&lb.h_acc, (cap + 2) * sizeof(unsigned long long)));
+    CK(cudaEventCreateWithFlags(&lb.consumed, cudaEventDisableTiming));
     lb.cap = cap;
     return SIEVE_OK;
 }
@@ -146,7 +147,22 @@ void free_launch_buffers(sieve_ctx *ctx, LaunchBuffers &lb) {
     if (lb.d_acc) dev_free(ctx, lb.d_acc, lb.cap + 2);
     if (lb.h_block) cudaFreeHost(lb.h_block);
     if (lb.h_acc) cudaFreeHost(lb.h_acc);
+    if (lb.consumed) cudaEventDestroy(lb.consumed);
     lb = LaunchBuffers();
+}
+
+int block_wait(sieve_ctx *ctx, LaunchBuffers &lb) {
+    if (lb.consumed) CK(cudaEventSynchronize(lb.consumed));
+    return SIEVE_OK;
+}
+
+// After the copies of lb's pinned block: mark it consumed (not inside a graph
+// capture, whose copies run at replay, after which the caller synchronises).
+static int mark_consumed(sieve_ctx *ctx, LaunchBuffers &lb, cudaStream_t stream) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(stream, &st));
+    if (st == cudaStreamCaptureStatusNone && lb.consumed) CK(cudaEventRecord(lb.consumed, stream));
+    return SIEVE_OK;
 }
 
 int alloc_compact_scratch(sieve_ctx *ctx, CompactScratch &cs, size_t tiles) {
@@ -401,6 +417,8 @@ int enqueue_launch(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int m
         CK(cudaMemcpyAsync(lb.d_mr(), lb.h_mr(), n_list * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
         CK(cudaMemcpyAsync(lb.d_mrw(), lb.h_mrw(), (n_list + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
     }
+    int rc = mark_consumed(ctx, lb, stream);
+    if (rc) return rc;
     CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
     const SieveLaunch *d = reinterpret_cast<const SieveLaunch *>(lb.d_block);
     const uint32_t smem = reinterpret_cast<const SieveLaunch *>(lb.h_block)->seg_bytes;  // the largest segment
@@ -521,6 +539,8 @@ int prepare_launch210(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size
 // Block copy, accumulator clear and the mod-210 sieve over `grid` CTAs.
 int enqueue_launch210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, LaunchBuffers &lb, size_t m, int grid) {
     CK(cudaMemcpyAsync(lb.d_block, lb.h_block, kLaunchHeader + m * sizeof(RangeDesc), cudaMemcpyHostToDevice, stream));
+    int rc = mark_consumed(ctx, lb, stream);
+    if (rc) return rc;
     CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
     const uint32_t smem = (reinterpret_cast<const SieveLaunch *>(lb.h_block)->seg_bytes + 15) & ~15u;
     if (grid > 0)
@@ -536,6 +556,32 @@ int launch_ranges210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, Lau
     if (rc) return rc;
     const uint64_t grid = (uint64_t)ctx->num_sms * prm.ctas_per_sm;
     return enqueue_launch210(ctx, stream, prm, lb, m, (int)std::min<uint64_t>(grid, items));
+}
+
+// The same kernels as compact_with without the host read of the total: the
+// count goes to the device integer *n_dev and nothing waits for the stream.
+int compact_async(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
+                  uint64_t hi, void *out_dev, size_t cap, uint64_t *n_dev, int out64) {
+    const uint64_t nwords = bitmap_words_of(lo, hi);
+    const uint32_t two = (lo <= 2 && 2 < hi) ? 1 : 0;
+    const uint64_t ntiles = (nwords + kCompactTileWords - 1) / kCompactTileWords;
+    int rc = alloc_compact_scratch(ctx, cs, ntiles);
+    if (rc) return rc;
+    if (ntiles) {
+        CK(launch_tile_popc(bitmap_dev, nwords, cs.counts, ntiles, ctx->num_sms * 8, stream));
+        CK(launch_tile_scan(cs.counts, cs.offsets, ntiles, cs.d_total, stream));
+        if (out_dev) {
+            if (two) CK(launch_put_two_if_fits(out_dev, out64, cs.d_total, cap, stream));
+            CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, lo | 1, two, out_dev, out64, ctx->num_sms,
+                           stream, cs.d_total, cap));
+        }
+        CK(launch_store_count(cs.d_total, two, n_dev, stream));
+        return SIEVE_OK;
+    }
+    // no odd integer in the range: the list is [2] or empty
+    if (two && cap) CK(launch_put_two(out_dev, out64, stream));
+    CK(launch_store_count(nullptr, two, n_dev, stream));
+    return SIEVE_OK;
 }
 
 int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
@@ -632,7 +678,11 @@ int ensure_bitmap(sieve_ctx *ctx, size_t words) {
     return SIEVE_OK;
 }
 
+// Every single-range and batched call writes the context's pinned launch block
+// after this: it first waits until the block's last copy has run.
 int ensure_launch(sieve_ctx *ctx, size_t m) {
+    int rc = block_wait(ctx, ctx->lb);
+    if (rc) return rc;
     if (m <= ctx->lb.cap) return SIEVE_OK;
     drop_graphs(ctx);  // they reference the old buffers
     return alloc_launch_buffers(ctx, ctx->lb, m);
@@ -807,6 +857,8 @@ int batch_graph(sieve_ctx *ctx, int mode, size_t m, size_t m210, const RangeOver
 }
 
 int ensure_launch210(sieve_ctx *ctx, size_t m) {
+    int rc = block_wait(ctx, ctx->lb210);
+    if (rc) return rc;
     if (m <= ctx->lb210.cap) return SIEVE_OK;
     drop_graphs(ctx);  // they reference the old buffers
     return alloc_launch_buffers(ctx, ctx->lb210, m);
@@ -1128,6 +1180,45 @@ int sieve_list(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, size
 
 int sieve_list64(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out_dev, size_t cap, uint64_t *n) {
     return list_impl(ctx, lo, hi, out_dev, cap, n, 1);
+}
+
+int sieve_bitmap_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev, size_t out_words,
+                     uint64_t *count_dev) {
+    if (!ctx) return SIEVE_EINVAL;
+    if (!count_dev) return fail(ctx, SIEVE_EINVAL, "null count");
+    int rc = check_range(ctx, lo, hi);
+    if (rc) return rc;
+    if ((rc = set_device(ctx))) return rc;
+    const uint64_t need = bitmap_words_of(lo, hi);
+    if (out_words < need) return fail(ctx, SIEVE_ETRUNC, "bitmap capacity too small");
+    if (need && !out_dev) return fail(ctx, SIEVE_EINVAL, "null bitmap");
+    if (lo == hi) {
+        CK(launch_store_count(nullptr, 0, count_dev, ctx->stream));
+        return SIEVE_OK;
+    }
+    rc = ensure_launch(ctx, 1);
+    if (rc) return rc;
+    const Params prm = single_range_params(ctx, lo, hi);
+    ctx->lb.h_ranges()[0] = plan_range(ctx, lo, hi, prm.seg_bytes, kModeBitmap, out_dev);
+    rc = launch_ranges(ctx, ctx->stream, prm, kModeBitmap, ctx->lb, 1, &ctx->buckets, &ctx->cursors);
+    if (rc) return rc;
+    // the count, or UINT64_MAX if a bucket list overflowed or a device-side wait gave up
+    CK(launch_finalize_count(ctx->lb.d_acc + 1, reinterpret_cast<const unsigned *>(ctx->lb.d_acc + 2), count_dev,
+                             ctx->stream));
+    return SIEVE_OK;
+}
+
+int sieve_compact_dev(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo, uint64_t hi, uint32_t *out_dev,
+                      size_t cap, uint64_t *n_dev) {
+    if (!ctx) return SIEVE_EINVAL;
+    if (!n_dev) return fail(ctx, SIEVE_EINVAL, "null n");
+    int rc = check_range(ctx, lo, hi);
+    if (rc) return rc;
+    if (hi > (1ull << 32)) return fail(ctx, SIEVE_ERANGE, "uint32 list needs hi <= 2^32");
+    if (bitmap_words_of(lo, hi) && !bitmap_dev) return fail(ctx, SIEVE_EINVAL, "null bitmap");
+    if (!out_dev && cap) return fail(ctx, SIEVE_EINVAL, "null output with a nonzero capacity");
+    if ((rc = set_device(ctx))) return rc;
+    return compact_async(ctx, ctx->stream, ctx->cs, bitmap_dev, lo, hi, out_dev, cap, n_dev, 0);
 }
 
 int sieve_compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo, uint64_t hi, uint32_t *out_dev,

@@ -252,6 +252,17 @@ cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t 
 }
 
 namespace {
+__global__ void k_store_count(const unsigned long long *total, uint32_t add, uint64_t *n) {
+    *n = (total ? *total : 0ull) + add;
+}
+}  // namespace
+
+cudaError_t launch_store_count(const unsigned long long *total, uint32_t add, uint64_t *n, cudaStream_t stream) {
+    k_store_count<<<1, 1, 0, stream>>>(total, add, n);
+    return cudaGetLastError();
+}
+
+namespace {
 // out[0] = 2 when the list fits: *total + 1 <= cap.
 template <typename T>
 __global__ void k_put_two_if_fits(T *out, const unsigned long long *total, uint64_t cap) {
