@@ -475,7 +475,8 @@ def _plain_same_integers(sv, lo, n, reps=3):
     import torch
     out = torch.zeros(1, dtype=torch.int64, device="cuda")
     ms = _event_ms(lambda: sv.count_dev(lo, lo + n, out), reps, torch.cuda.current_stream())
-    return {"value": n / (ms * 1e-3), "unit": METRIC, "range": [lo, lo + n], "ms": ms}
+    return {"value": n / (ms * 1e-3), "unit": METRIC, "range": [lo, lo + n], "ms": ms,
+            "clears_per_s": sv.crossing_work(lo, lo + n) / (ms * 1e-3)}
 
 
 def batched_measure(steps=10, warmup=3, cpu=True, tuned=True):
@@ -517,6 +518,9 @@ def batched_measure(steps=10, warmup=3, cpu=True, tuned=True):
                       "integers": units, "timing": "host wall clock around sieve_batch_count "
                                                    "(host arrays in, host counts out)"},
            "vs_plain": (units / dt) / plain["value"],
+           # in bit-clears (the kernel's own work): the batch's ranges high up need more
+           # base primes per integer than the plain range from the median start
+           "vs_plain_clears": (clears / dt) / plain["clears_per_s"],
            "plain_single_range": plain,
            "one_call_per_interval": {"value": units / one_by_one, "unit": METRIC},
            "roofline": _op_roofline(clears, dt, n_sms, peaks, peak_kind, probe, atomics),
@@ -826,10 +830,11 @@ def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000
             reqs = served_stream(rate=rate, n=n, seed=1205)
             all_reqs.append(reqs)
             results.append(_serve_stream(srv, reqs, rate))
-        count_only = []
+        count_only, co_reqs = [], []
         for rate in count_only_rates:
             n = requests or int(min(10000, max(300, rate)))
-            count_only.append(_serve_stream(srv, served_stream(rate=rate, n=n, seed=1205, list_frac=0.0), rate))
+            co_reqs.append(served_stream(rate=rate, n=n, seed=1205, list_frac=0.0))
+            count_only.append(_serve_stream(srv, co_reqs[-1], rate))
     best_i = max(range(len(results)), key=lambda i: results[i]["integers_per_s"])
     best = results[best_i]
     reqs = all_reqs[best_i]
@@ -842,13 +847,17 @@ def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000
     clears = sum(sv.crossing_work(r.lo, r.hi) for r in reqs)
     atomics = sum(sv.crossing_work(r.lo, r.hi, _atomic_pmin(sv)) for r in reqs)
     probe = gb.sieve_probe(sv.ctx, gb.SIEVE_PROBE_SMEM_AND_CONFLICT_FREE)
-    sv.close()
     d2h_line = {"bound": "d2h", "op": "list results (uint64) copied to pinned host memory",
                 "achieved": best["list_bytes_to_host"] / best["wall_s"] / 1e9, "peak": d2h, "unit": "GB/s",
                 "frac": best["list_bytes_to_host"] / best["wall_s"] / 1e9 / d2h,
                 "peak_basis": "pinned device-to-host copy, 2 GiB, best of 3 (measured in this run)",
                 "bytes": best["list_bytes_to_host"]}
     co_best = max(count_only, key=lambda r: r["integers_per_s"]) if count_only else None
+    if co_best is not None:
+        # the same comparison in the kernel's own work: narrow requests need fewer base primes
+        # per integer than one long range from the median start, so integers/s flatter them
+        co_clears = sum(sv.crossing_work(r.lo, r.hi) for r in co_reqs[count_only.index(co_best)])
+        co_clears_per_s = co_clears / co_best["wall_s"]
     out = {"value": best["integers_per_s"], "unit": METRIC,
            "config": {"workload": "served: seeded Poisson stream, 80% count / 20% list, lo log-uniform "
                                   "[0, 1e12], w log-uniform [1e4, 1e9]", "seed": 1205,
@@ -856,6 +865,7 @@ def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000
                       "timing": "host wall clock from the first arrival to the last result"},
            "rates": results,
            "vs_plain": best["integers_per_s"] / plain["value"],
+           "vs_plain_clears": clears / best["wall_s"] / plain["clears_per_s"],
            "plain_single_range": plain,
            "roofline": d2h_line,
            "roofline_sieve": _op_roofline(clears, best["wall_s"], n_sms, peaks, peak_kind, probe, atomics),
@@ -863,8 +873,11 @@ def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000
     if co_best is not None:
         out["count_only"] = {"value": co_best["integers_per_s"], "unit": METRIC,
                              "vs_plain": co_best["integers_per_s"] / plain["value"],
+                             "clears_per_s": co_clears_per_s,
+                             "vs_plain_clears": co_clears_per_s / plain["clears_per_s"],
                              "workload": "the same stream with list_frac 0 (every request a count)",
                              "rates": count_only}
+    sv.close()
     if cpu:
         out["cpu_baseline"] = served_cpu_baseline(out)
     return out
@@ -872,7 +885,8 @@ def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000
 
 def run_served(args):
     rates = [float(r) for r in args.rates.split(",")]
-    out = served_measure(rates, args.requests)
+    co = tuple(float(r) for r in args.count_only_rates.split(",")) if args.count_only_rates else ()
+    out = served_measure(rates, args.requests, count_only_rates=co, cpu=not args.no_cpu_baseline)
     line = {"metric": METRIC, "value": out["value"], "unit": METRIC, "n_gpus": 1, "steps": len(rates),
             "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": out["config"]}
@@ -908,6 +922,8 @@ def main():
     ap.add_argument("--rates", default="100,300,1000,3000,10000,30000", help="served: offered loads, req/s")
     ap.add_argument("--default-rates", default="1000,10000,30000",
                     help="served rates of the sub-object in the default line")
+    ap.add_argument("--count-only-rates", default="60000,120000,240000",
+                    help="served: offered loads of the count-only stream, req/s (empty: none)")
     ap.add_argument("--no-sub", action="store_true", help="default line without the batched/served sub-objects")
     ap.add_argument("--requests", type=int, default=0,
                     help="served: requests per rate (0: 1 s of arrivals, between 300 and 10000)")
@@ -941,7 +957,8 @@ def main():
             # followed it from 3 to 17 ms); the served stream, the workload most sensitive to
             # what ran before it in the process, comes first.
             rates = [float(r) for r in args.default_rates.split(",")]
-            sub["served"] = served_measure(rates, cpu=False)
+            co = tuple(float(r) for r in args.count_only_rates.split(",")) if args.count_only_rates else ()
+            sub["served"] = served_measure(rates, cpu=False, count_only_rates=co)
             sub["batched"] = batched_measure(args.steps, args.warmup, cpu=False)
             sub["pi1e7"] = outputs_measure(0, 10**7, "[0, 10^7): count, odd-only bitmap and u32 prime list",
                                            True, args.steps, args.warmup, cpu=False)
