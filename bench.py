@@ -715,10 +715,12 @@ def run_outputs(args, lo, hi, name, with_count):
     return 0
 
 
-def _serve_stream(srv, reqs, rate):
+def _serve_stream(srv, reqs, rate, offsets=False):
     """Play one request stream against the server srv (arrivals at their times, admission
     retried while full), collect results through the completion queue and release them.
-    Returns the per-rate record (counters as differences over the stream)."""
+    List requests ask for uint64 primes, or with offsets=True for uint32 offsets from lo
+    (SIEVE_REQ_LIST_OFFSETS).  Returns the per-rate record (counters as differences over
+    the stream)."""
     import queue
     import threading
 
@@ -758,7 +760,8 @@ def _serve_stream(srv, reqs, rate):
         now = time.perf_counter() - t0
         if r.arrival_s > now:
             time.sleep(r.arrival_s - now)
-        kind = gb.SIEVE_REQ_LIST if r.kind == "list" else gb.SIEVE_REQ_COUNT
+        list_kind = gb.SIEVE_REQ_LIST_OFFSETS if offsets else gb.SIEVE_REQ_LIST
+        kind = list_kind if r.kind == "list" else gb.SIEVE_REQ_COUNT
         rc, t = srv.submit(r.lo, r.hi, kind)
         give_up = time.perf_counter() + 120
         while rc == gb.SIEVE_EBUSY:  # admission is full: retry (bounded)
@@ -785,7 +788,8 @@ def _serve_stream(srv, reqs, rate):
             by_kind[kd] = {"n": len(xs), "p50_ms": float(np.percentile(xs, 50)) / 1e3,
                            "p99_ms": float(np.percentile(xs, 99)) / 1e3}
     lat_all = [x for x, _, _ in lat]
-    list_bytes = 8 * sum(c for _, t, c in lat if kinds[t] == "list")  # uint64 results copied to the host
+    # results copied to the host: uint64 primes or uint32 offsets
+    list_bytes = (4 if offsets else 8) * sum(c for _, t, c in lat if kinds[t] == "list")
     return {"offered_req_s": rate, "requests": len(reqs), "integers_per_s": ints / wall,
             "p50_ms": float(np.percentile(lat_all, 50)) / 1e3, "p99_ms": float(np.percentile(lat_all, 99)) / 1e3,
             "by_kind": by_kind, "wall_s": wall, "busy_retries": rejected, "ticks": st["ticks"] - st0["ticks"],
@@ -809,14 +813,15 @@ def _d2h_gbs():
     return (2 << 30) / best / 1e9
 
 
-def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000.0), **server_kw):
+def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000.0), offsets_rates=(), **server_kw):
     """A seeded Poisson stream (80% count, 20% list; lo log-uniform in [0, 1e12], width
     log-uniform in [1e4, 1e9]) at each offered rate through the request server:
     p50/p99 latency (submit to result on the host) and integers/s, against the plain
     single-range sieve of the same number of integers at the stream's median start.  The
     list results (uint64 primes) go to host memory, so the mixed stream is bound by the
     device-to-host copy bandwidth: its roofline is that copy.  The same stream with count
-    requests only (the sieve side of the server) is reported beside it."""
+    requests only (the sieve side of the server) is reported beside it, and the same mixed
+    stream with its lists as uint32 offsets from lo (half the bytes over the link)."""
     import torch
     import paper_1205_4883_gb300 as gb
     from paper_1205_4883_gb300.workloads import served_stream
@@ -835,6 +840,11 @@ def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000
             n = requests or int(min(10000, max(300, rate)))
             co_reqs.append(served_stream(rate=rate, n=n, seed=1205, list_frac=0.0))
             count_only.append(_serve_stream(srv, co_reqs[-1], rate))
+        offs, off_reqs = [], []
+        for rate in offsets_rates:
+            n = requests or int(min(10000, max(300, rate)))
+            off_reqs.append(served_stream(rate=rate, n=n, seed=1205))
+            offs.append(_serve_stream(srv, off_reqs[-1], rate, offsets=True))
     best_i = max(range(len(results)), key=lambda i: results[i]["integers_per_s"])
     best = results[best_i]
     reqs = all_reqs[best_i]
@@ -877,6 +887,20 @@ def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000
                              "vs_plain_clears": co_clears_per_s / plain["clears_per_s"],
                              "workload": "the same stream with list_frac 0 (every request a count)",
                              "rates": count_only}
+    if offs:
+        ob = max(range(len(offs)), key=lambda i: offs[i]["integers_per_s"])
+        o_best = offs[ob]
+        o_clears = sum(sv.crossing_work(r.lo, r.hi) for r in off_reqs[ob])
+        o_gbs = o_best["list_bytes_to_host"] / o_best["wall_s"] / 1e9
+        out["offsets"] = {"value": o_best["integers_per_s"], "unit": METRIC,
+                          "vs_plain": o_best["integers_per_s"] / plain["value"],
+                          "vs_plain_clears": o_clears / o_best["wall_s"] / plain["clears_per_s"],
+                          "workload": "the same mixed stream, list requests as SIEVE_REQ_LIST_OFFSETS "
+                                      "(uint32 offsets from lo)",
+                          "roofline": {"bound": "d2h", "op": "list results (uint32 offsets) copied to pinned "
+                                       "host memory", "achieved": o_gbs, "peak": d2h, "unit": "GB/s",
+                                       "frac": o_gbs / d2h, "bytes": o_best["list_bytes_to_host"]},
+                          "rates": offs}
     sv.close()
     if cpu:
         out["cpu_baseline"] = served_cpu_baseline(out)
@@ -886,7 +910,9 @@ def served_measure(rates, requests=0, cpu=True, count_only_rates=(30000.0, 60000
 def run_served(args):
     rates = [float(r) for r in args.rates.split(",")]
     co = tuple(float(r) for r in args.count_only_rates.split(",")) if args.count_only_rates else ()
-    out = served_measure(rates, args.requests, count_only_rates=co, cpu=not args.no_cpu_baseline)
+    of = tuple(float(r) for r in args.offsets_rates.split(",")) if args.offsets_rates else ()
+    out = served_measure(rates, args.requests, count_only_rates=co, offsets_rates=of,
+                         cpu=not args.no_cpu_baseline)
     line = {"metric": METRIC, "value": out["value"], "unit": METRIC, "n_gpus": 1, "steps": len(rates),
             "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": out["config"]}
@@ -924,6 +950,8 @@ def main():
                     help="served rates of the sub-object in the default line")
     ap.add_argument("--count-only-rates", default="60000,120000,240000",
                     help="served: offered loads of the count-only stream, req/s (empty: none)")
+    ap.add_argument("--offsets-rates", default="30000,60000",
+                    help="served: offered loads of the mixed stream with offset lists, req/s (empty: none)")
     ap.add_argument("--no-sub", action="store_true", help="default line without the batched/served sub-objects")
     ap.add_argument("--requests", type=int, default=0,
                     help="served: requests per rate (0: 1 s of arrivals, between 300 and 10000)")
@@ -958,7 +986,8 @@ def main():
             # what ran before it in the process, comes first.
             rates = [float(r) for r in args.default_rates.split(",")]
             co = tuple(float(r) for r in args.count_only_rates.split(",")) if args.count_only_rates else ()
-            sub["served"] = served_measure(rates, cpu=False, count_only_rates=co)
+            of = tuple(float(r) for r in args.offsets_rates.split(",")) if args.offsets_rates else ()
+            sub["served"] = served_measure(rates, cpu=False, count_only_rates=co, offsets_rates=of)
             sub["batched"] = batched_measure(args.steps, args.warmup, cpu=False)
             sub["pi1e7"] = outputs_measure(0, 10**7, "[0, 10^7): count, odd-only bitmap and u32 prime list",
                                            True, args.steps, args.warmup, cpu=False)

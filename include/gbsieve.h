@@ -239,6 +239,11 @@ typedef struct sieve_server sieve_server;
 
 #define SIEVE_REQ_COUNT 0 /* result: the count */
 #define SIEVE_REQ_LIST  1 /* result: the count and the ascending primes (uint64, host) */
+#define SIEVE_REQ_LIST_OFFSETS 2 /* result: the count and the ascending offsets p - lo of
+                                    the primes (uint32, host): half the bytes of a list,
+                                    for ranges with hi - lo <= 2^32 (else SIEVE_ERANGE at
+                                    submit).  Results cross to the host over a link of
+                                    about 193 GB/s, which bounds a stream of list requests */
 
 typedef struct {
     uint32_t max_requests;     /* requests admitted and not yet released (0: 1024) */
@@ -255,7 +260,7 @@ typedef struct {
 
 typedef struct {
     uint64_t lo, hi; /* the range [lo, hi), hi <= the context's hi_max */
-    int32_t kind;    /* SIEVE_REQ_COUNT or SIEVE_REQ_LIST */
+    int32_t kind;    /* SIEVE_REQ_COUNT, SIEVE_REQ_LIST or SIEVE_REQ_LIST_OFFSETS */
     int32_t reserved;
 } sieve_req;
 
@@ -268,6 +273,8 @@ typedef struct {
                                pinned memory (a 1 GiB arena the results are copied into by
                                DMA) unless the arena was full, then ordinary heap memory */
     double latency_us;      /* from submit to the result being ready on the host */
+    const uint32_t *offsets; /* SIEVE_REQ_LIST_OFFSETS: `count` offsets p - lo, memory as for
+                               primes; else NULL */
 } sieve_result;
 
 typedef struct {

@@ -73,7 +73,8 @@ class sieve_req(ctypes.Structure):
 
 class sieve_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("count", _u64),
-                ("primes", ctypes.POINTER(_u64)), ("latency_us", ctypes.c_double)]
+                ("primes", ctypes.POINTER(_u64)), ("latency_us", ctypes.c_double),
+                ("offsets", ctypes.POINTER(ctypes.c_uint32))]
 
 
 class sieve_server_counters(ctypes.Structure):
@@ -89,6 +90,7 @@ class sieve_range_params(ctypes.Structure):
 
 SIEVE_REQ_COUNT = 0
 SIEVE_REQ_LIST = 1
+SIEVE_REQ_LIST_OFFSETS = 2
 MR_NEVER = 0xFFFFFFFF
 
 # name -> (restype, argtypes)
@@ -422,20 +424,26 @@ def sieve_server_submit(srv: int, lo: int, hi: int, kind: int = SIEVE_REQ_COUNT)
 
 def sieve_server_poll(srv: int, ticket: int, timeout_us: int = -1, copy_primes: bool = True):
     """Returns (rc, result dict or None); rc SIEVE_OK or SIEVE_ETIMEOUT (others raise).
-    A list result's primes are copied out of the server's memory (unless copy_primes
-    is False, when only the count is returned)."""
+    A list result's primes (or, for SIEVE_REQ_LIST_OFFSETS, their uint32 offsets from lo,
+    under "offsets") are copied out of the server's memory (unless copy_primes is False,
+    when only the count is returned)."""
     res = sieve_result()
     rc = load_library().sieve_server_poll(srv, ticket, ctypes.byref(res), timeout_us)
     _check(0, rc, allow=(SIEVE_ETIMEOUT,))
     if rc != SIEVE_OK:
         return rc, None
     out = {"status": res.status, "kind": res.kind, "count": int(res.count), "latency_us": res.latency_us,
-           "primes": None}
+           "primes": None, "offsets": None}
     if copy_primes and res.kind == SIEVE_REQ_LIST and res.status == SIEVE_OK:
         import numpy as np
         n = int(res.count)
         out["primes"] = (np.ctypeslib.as_array(res.primes, shape=(n,)).copy() if n
                          else np.zeros(0, dtype=np.uint64))
+    if copy_primes and res.kind == SIEVE_REQ_LIST_OFFSETS and res.status == SIEVE_OK:
+        import numpy as np
+        n = int(res.count)
+        out["offsets"] = (np.ctypeslib.as_array(res.offsets, shape=(n,)).copy() if n
+                          else np.zeros(0, dtype=np.uint32))
     return rc, out
 
 

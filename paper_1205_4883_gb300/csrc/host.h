@@ -181,10 +181,11 @@ int launch_ranges210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, Lau
 int launch_ranges(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
                   BucketStore *bs, CursorStore *cs = nullptr, const RangeOverride *ro = nullptr);
 
-// Compact the odd-only bitmap of [lo, hi) into out_dev (uint32 or uint64).
-// *n = primes in the range (2 included); SIEVE_ETRUNC if cap < *n.
-// Synchronises `stream`.
+// Compact the odd-only bitmap of [lo, hi) into out_dev (uint32 or uint64): the
+// values p - sub (sub = 0: the primes; sub = lo: their offsets from lo, which a
+// uint32 list can hold whenever hi - lo <= 2^32).  *n = primes in the range (2
+// included); SIEVE_ETRUNC if cap < *n.  Synchronises `stream`.
 int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
-                 uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64);
+                 uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64, uint64_t sub = 0);
 
 }  // namespace gbs

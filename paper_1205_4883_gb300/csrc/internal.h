@@ -172,10 +172,11 @@ cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t 
                         uint64_t ntiles, uint64_t o0, uint32_t base_index, void *out,
                         int out64, int num_sms, cudaStream_t stream,
                         const unsigned long long *total = nullptr, uint64_t cap = 0);
-cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream);
-// out[0] = 2 if *total + 1 <= cap.
+// out[0] = 2 - sub (sub: the value base a list is written relative to, 0 for primes).
+cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream, uint64_t sub = 0);
+// out[0] = 2 - sub if *total + 1 <= cap.
 cudaError_t launch_put_two_if_fits(void *out, int out64, const unsigned long long *total, uint64_t cap,
-                                   cudaStream_t stream);
+                                   cudaStream_t stream, uint64_t sub = 0);
 // *out = *count, or UINT64_MAX when *overflow is set.
 cudaError_t launch_finalize_count(const unsigned long long *count, const unsigned *overflow, uint64_t *out,
                                   cudaStream_t stream);

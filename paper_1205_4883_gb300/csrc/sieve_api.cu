@@ -585,7 +585,7 @@ int compact_async(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const
 }
 
 int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
-                 uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64) {
+                 uint64_t hi, void *out_dev, size_t cap, uint64_t *n, int out64, uint64_t sub) {
     if (!out_dev && cap) return fail(ctx, SIEVE_EINVAL, "null output with a nonzero capacity");
     const uint64_t nwords = bitmap_words_of(lo, hi);
     const uint32_t two = (lo <= 2 && 2 < hi) ? 1 : 0;
@@ -600,9 +600,9 @@ int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const 
         CK(launch_tile_popc(bitmap_dev, nwords, cs.counts, ntiles, grid, stream));
         CK(launch_tile_scan(cs.counts, cs.offsets, ntiles, cs.d_total, stream));
         if (out_dev) {
-            if (two) CK(launch_put_two_if_fits(out_dev, out64, cs.d_total, cap, stream));
-            CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, lo | 1, two, out_dev, out64, ctx->num_sms,
-                           stream, cs.d_total, cap));
+            if (two) CK(launch_put_two_if_fits(out_dev, out64, cs.d_total, cap, stream, sub));
+            CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, (lo | 1) - sub, two, out_dev, out64,
+                           ctx->num_sms, stream, cs.d_total, cap));
         }
         CK(cudaMemcpyAsync(cs.h_total, cs.d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
@@ -612,7 +612,7 @@ int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const 
     if (*n > cap) return fail(ctx, SIEVE_ETRUNC, "output capacity below the prime count");  // nothing written
     if (*n == 0 || ntiles) return SIEVE_OK;
     // no odd integer in the range: the list is [2]
-    CK(launch_put_two(out_dev, out64, stream));
+    CK(launch_put_two(out_dev, out64, stream, sub));
     CK(cudaStreamSynchronize(stream));
     return SIEVE_OK;
 }

@@ -263,19 +263,20 @@ cudaError_t launch_store_count(const unsigned long long *total, uint32_t add, ui
 }
 
 namespace {
-// out[0] = 2 when the list fits: *total + 1 <= cap.
+// out[0] = two (the prime 2, less the value base) when the list fits: *total + 1 <= cap.
 template <typename T>
-__global__ void k_put_two_if_fits(T *out, const unsigned long long *total, uint64_t cap) {
-    if (*total + 1 <= cap) out[0] = (T)2;
+__global__ void k_put_two_if_fits(T *out, const unsigned long long *total, uint64_t cap, T two) {
+    if (*total + 1 <= cap) out[0] = two;
 }
 }  // namespace
 
 cudaError_t launch_put_two_if_fits(void *out, int out64, const unsigned long long *total, uint64_t cap,
-                                   cudaStream_t stream) {
+                                   cudaStream_t stream, uint64_t sub) {
     if (out64)
-        k_put_two_if_fits<uint64_t><<<1, 1, 0, stream>>>(static_cast<uint64_t *>(out), total, cap);
+        k_put_two_if_fits<uint64_t><<<1, 1, 0, stream>>>(static_cast<uint64_t *>(out), total, cap, 2 - sub);
     else
-        k_put_two_if_fits<uint32_t><<<1, 1, 0, stream>>>(static_cast<uint32_t *>(out), total, cap);
+        k_put_two_if_fits<uint32_t><<<1, 1, 0, stream>>>(static_cast<uint32_t *>(out), total, cap,
+                                                         (uint32_t)(2 - sub));
     return cudaGetLastError();
 }
 

@@ -907,7 +907,7 @@ __global__ void k_magic(const uint32_t *primes, uint64_t *magic, uint64_t n) {
 // ---------------------------------------------------------------- compaction
 
 template <typename T>
-__global__ void k_put_two(T *out) { out[0] = (T)2; }
+__global__ void k_put_two(T *out, T two) { out[0] = two; }
 
 __global__ void k_finalize_count(const unsigned long long *count, const unsigned *overflow, uint64_t *out) {
     *out = *overflow ? ~0ull : *count;
@@ -960,11 +960,11 @@ cudaError_t launch_finalize_count(const unsigned long long *count, const unsigne
     return cudaGetLastError();
 }
 
-cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream) {
+cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream, uint64_t sub) {
     if (out64)
-        k_put_two<uint64_t><<<1, 1, 0, stream>>>(static_cast<uint64_t *>(out));
+        k_put_two<uint64_t><<<1, 1, 0, stream>>>(static_cast<uint64_t *>(out), 2 - sub);
     else
-        k_put_two<uint32_t><<<1, 1, 0, stream>>>(static_cast<uint32_t *>(out));
+        k_put_two<uint32_t><<<1, 1, 0, stream>>>(static_cast<uint32_t *>(out), (uint32_t)(2 - sub));
     return cudaGetLastError();
 }
 

@@ -48,8 +48,8 @@ struct Req {
     uint64_t *d_list = nullptr;
     uint64_t list_cap = 0;
     size_t arena_off = 0, arena_bytes = 0;
-    std::unique_ptr<uint64_t[]> primes;  // list result on the heap (when the pinned arena is full)
-    uint64_t *h_primes = nullptr;        // the list result handed out: pinned arena or `primes`
+    std::unique_ptr<unsigned char[]> heap;  // list result on the heap (when the pinned arena is full)
+    void *h_list = nullptr;                 // the list result handed out: pinned arena or `heap`
     size_t harena_off = 0, harena_bytes = 0;
     int status = SIEVE_OK;
     bool done = false;
@@ -185,38 +185,45 @@ void complete(sieve_server *srv, Req *r, int status) {
 constexpr size_t kBounceWords = 2u << 20;  // 16 MiB of uint64 per finisher
 constexpr size_t kHostArenaBytes = 1ull << 30;  // pinned host memory for list results (default)
 
+// Bytes per list element: uint64 primes, or uint32 offsets from lo.
+size_t list_elem(const Req *r) { return r->kind == SIEVE_REQ_LIST_OFFSETS ? 4 : 8; }
+
 // Called without the lock: compaction of a finished list request into its
-// device list, then one DMA copy into the pinned host arena -- or, when the
-// arena has no room, a chunked copy to the heap through the pinned buffer.
+// device list (the primes, or their offsets from lo), then one DMA copy into the
+// pinned host arena -- or, when the arena has no room, a chunked copy to the
+// heap through the pinned buffer.
 int finish_list(sieve_server *srv, Finisher &f, Req *r) {
     uint64_t n = 0;
-    int rc = compact_with(srv->view, f.stream, f.cs, r->d_bitmap, r->lo, r->hi, r->d_list, r->list_cap, &n, 1);
+    const bool offsets = r->kind == SIEVE_REQ_LIST_OFFSETS;
+    const size_t es = list_elem(r);
+    int rc = compact_with(srv->view, f.stream, f.cs, r->d_bitmap, r->lo, r->hi, r->d_list, r->list_cap, &n,
+                          offsets ? 0 : 1, offsets ? r->lo : 0);
     if (rc) return rc;
     bool pinned = false;
     if (n && srv->host_arena.size) {
         std::lock_guard<std::mutex> lk(srv->mu);
-        pinned = srv->host_arena.alloc(n * sizeof(uint64_t), &r->harena_off);
-        if (pinned) r->harena_bytes = n * sizeof(uint64_t);
+        pinned = srv->host_arena.alloc(n * es, &r->harena_off);
+        if (pinned) r->harena_bytes = n * es;
     }
     if (pinned) {
-        r->h_primes = reinterpret_cast<uint64_t *>(srv->host_arena.base + r->harena_off);
-        cudaError_t e = cudaMemcpyAsync(r->h_primes, r->d_list, n * sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                                        f.stream);
+        r->h_list = srv->host_arena.base + r->harena_off;
+        cudaError_t e = cudaMemcpyAsync(r->h_list, r->d_list, n * es, cudaMemcpyDeviceToHost, f.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(f.stream);
         if (e != cudaSuccess) return cuda_fail(srv->view, e, "list copy");
         r->count = n;
         return SIEVE_OK;
     }
-    r->primes.reset(new (std::nothrow) uint64_t[n ? n : 1]);
-    if (!r->primes) return SIEVE_ENOMEM;
-    r->h_primes = r->primes.get();
-    for (uint64_t done = 0; done < n; done += kBounceWords) {
-        const uint64_t k = std::min<uint64_t>(kBounceWords, n - done);
-        cudaError_t e = cudaMemcpyAsync(f.bounce, r->d_list + done, k * sizeof(uint64_t),
-                                        cudaMemcpyDeviceToHost, f.stream);
+    r->heap.reset(new (std::nothrow) unsigned char[n ? n * es : 8]);
+    if (!r->heap) return SIEVE_ENOMEM;
+    r->h_list = r->heap.get();
+    const unsigned char *src = reinterpret_cast<const unsigned char *>(r->d_list);
+    const uint64_t chunk = kBounceWords * 8 / es;  // elements per pass through the bounce buffer
+    for (uint64_t done = 0; done < n; done += chunk) {
+        const uint64_t k = std::min<uint64_t>(chunk, n - done);
+        cudaError_t e = cudaMemcpyAsync(f.bounce, src + done * es, k * es, cudaMemcpyDeviceToHost, f.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(f.stream);
         if (e != cudaSuccess) return cuda_fail(srv->view, e, "list copy");
-        std::memcpy(r->primes.get() + done, f.bounce, k * sizeof(uint64_t));
+        std::memcpy(r->heap.get() + done * es, f.bounce, k * es);
     }
     r->count = n;
     return SIEVE_OK;
@@ -233,7 +240,7 @@ void harvest(sieve_server *srv, Tick &t) {
             r->done_segs += run.seg_b - run.seg_a;
             if (r->done_segs != r->plan.nseg) continue;
             srv->active.erase(std::remove(srv->active.begin(), srv->active.end(), r), srv->active.end());
-            if (r->kind == SIEVE_REQ_LIST) {
+            if (r->kind != SIEVE_REQ_COUNT) {
                 srv->to_finish.push_back(r);
                 srv->cv_finish.notify_one();
             } else {
@@ -286,7 +293,7 @@ int launch_tick(sieve_server *srv, Tick &t) {
         Req *r = srv->active[(start + q) % n_act];
         if (r->next_seg >= r->plan.nseg) continue;
         const uint64_t take = std::min<uint64_t>({r->plan.nseg - r->next_seg, share, budget});
-        const int mode = r->kind == SIEVE_REQ_LIST ? kModeBitmap : kModeCount;
+        const int mode = r->kind != SIEVE_REQ_COUNT ? kModeBitmap : kModeCount;
         if (m[mode] >= t.lb[mode].cap) continue;
         t.lb[mode].h_ranges()[m[mode]++] = plan_run(srv, *r, r->next_seg, r->next_seg + take, mode);
         t.runs[mode].push_back(Run{r, r->next_seg, r->next_seg + take});
@@ -315,7 +322,7 @@ void fail_all(sieve_server *srv, int rc) {
     for (Tick &t : srv->ticks)
         for (auto &rs : t.runs) rs.clear();
     for (Req *r : srv->active) {
-        if (r->kind == SIEVE_REQ_LIST) srv->arena.release(r->arena_off, r->arena_bytes);
+        if (r->kind != SIEVE_REQ_COUNT) srv->arena.release(r->arena_off, r->arena_bytes);
         complete(srv, r, rc);
     }
     srv->active.clear();
@@ -453,15 +460,18 @@ int sieve_server_create(sieve_ctx *ctx, const sieve_server_cfg *cfg, sieve_serve
 
 int sieve_server_submit(sieve_server *srv, const sieve_req *req, uint64_t *ticket) {
     if (!srv || !req || !ticket) return SIEVE_EINVAL;
-    if (req->lo > req->hi || (req->kind != SIEVE_REQ_COUNT && req->kind != SIEVE_REQ_LIST)) return SIEVE_EINVAL;
+    if (req->lo > req->hi || (req->kind != SIEVE_REQ_COUNT && req->kind != SIEVE_REQ_LIST &&
+                              req->kind != SIEVE_REQ_LIST_OFFSETS))
+        return SIEVE_EINVAL;
     if (req->hi > srv->view->hi_max) return SIEVE_ERANGE;
+    if (req->kind == SIEVE_REQ_LIST_OFFSETS && req->hi - req->lo > (1ull << 32)) return SIEVE_ERANGE;
     std::unique_ptr<Req> r(new (std::nothrow) Req);
     if (!r) return SIEVE_ENOMEM;
     r->lo = req->lo;
     r->hi = req->hi;
     r->kind = req->kind;
     r->t_submit = Clock::now();
-    const int mode = r->kind == SIEVE_REQ_LIST ? kModeBitmap : kModeCount;
+    const int mode = r->kind != SIEVE_REQ_COUNT ? kModeBitmap : kModeCount;
     r->plan = plan_range(srv->view, r->lo, r->hi, srv->view->params.seg_bytes, mode, nullptr);
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) return SIEVE_EINVAL;
@@ -469,7 +479,7 @@ int sieve_server_submit(sieve_server *srv, const sieve_req *req, uint64_t *ticke
         srv->st.rejected++;
         return SIEVE_EBUSY;
     }
-    if (r->kind == SIEVE_REQ_LIST && r->hi > r->lo) {
+    if (r->kind != SIEVE_REQ_COUNT && r->hi > r->lo) {
         const uint64_t words = bitmap_words_of(r->lo, r->hi);
         r->list_cap = prime_count_bound(r->hi - r->lo);
         const size_t bm_bytes = ((words * 4 + 255) & ~(size_t)255);
@@ -514,7 +524,9 @@ int sieve_server_poll(sieve_server *srv, uint64_t ticket, sieve_result *res, int
     res->status = r->status;
     res->kind = r->kind;
     res->count = r->count;
-    res->primes = (r->kind == SIEVE_REQ_LIST && r->status == SIEVE_OK) ? r->h_primes : nullptr;
+    const bool ok = r->status == SIEVE_OK;
+    res->primes = (r->kind == SIEVE_REQ_LIST && ok) ? static_cast<const uint64_t *>(r->h_list) : nullptr;
+    res->offsets = (r->kind == SIEVE_REQ_LIST_OFFSETS && ok) ? static_cast<const uint32_t *>(r->h_list) : nullptr;
     res->latency_us = r->latency_us;
     return SIEVE_OK;
 }

@@ -109,6 +109,42 @@ def test_admission_and_errors(sv):
     assert e.value.code == gb.SIEVE_ENOENT
 
 
+def test_offset_lists_match_the_oracle(sv):
+    # SIEVE_REQ_LIST_OFFSETS: uint32 offsets p - lo; the same primes as a uint64 list of the
+    # same range, submitted in the same stream; ranges around 2, ragged ends, one at the top
+    # of the context's range and a 3e8-wide one (many tiles of the compaction)
+    ranges = [(0, 100), (1, 3), (2, 3), (3, 4), (0, 2), (10**12 - 10**6, 10**12),
+              (10**12 + 2 * 10**9 - 10**6 - 7, 10**12 + 2 * 10**9), (10**9 + 1, 10**9 + 3 * 10**8)]
+    ranges += [(r.lo, r.hi) for r in served_stream(rate=1000.0, n=20, seed=77, w_exp=(3, 7))]
+    with gb.Server(sv, max_device_bytes=4 << 30) as srv:
+        tickets = []
+        for lo, hi in ranges:
+            pair = []
+            for kind in (gb.SIEVE_REQ_LIST_OFFSETS, gb.SIEVE_REQ_LIST):
+                rc, t = srv.submit(lo, hi, kind)
+                assert rc == gb.SIEVE_OK
+                pair.append(t)
+            tickets.append(pair)
+        for (lo, hi), (t_off, t_list) in zip(ranges, tickets):
+            rc, off = srv.poll(t_off, timeout_us=60_000_000)
+            assert rc == gb.SIEVE_OK and off["status"] == gb.SIEVE_OK
+            rc, lst = srv.poll(t_list, timeout_us=60_000_000)
+            assert rc == gb.SIEVE_OK and lst["status"] == gb.SIEVE_OK
+            want = oracle.primes(lo, hi)
+            assert off["count"] == lst["count"] == len(want), (lo, hi)
+            assert off["primes"] is None and off["offsets"].dtype == np.uint32
+            assert np.array_equal(off["offsets"].astype(np.uint64) + np.uint64(lo), want), (lo, hi)
+            assert np.array_equal(lst["primes"], want), (lo, hi)
+            assert srv.release(t_off) == gb.SIEVE_OK and srv.release(t_list) == gb.SIEVE_OK
+        # offsets must fit in 32 bits: a range wider than 2^32 is refused at submit
+        with pytest.raises(gb.SieveError) as e:
+            srv.submit(0, 2**32 + 1, gb.SIEVE_REQ_LIST_OFFSETS)
+        assert e.value.code == gb.SIEVE_ERANGE
+        with pytest.raises(gb.SieveError) as e:
+            srv.submit(0, 10, 3)
+        assert e.value.code == gb.SIEVE_EINVAL
+
+
 def test_list_results_beyond_the_pinned_arena(sv):
     # four list results of ~48M primes (~385 MB each) held at once: the first ones land in
     # the 1 GiB pinned arena, the last one on the heap (bounce-buffer path); all exact
