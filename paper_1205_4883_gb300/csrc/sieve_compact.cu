@@ -57,48 +57,59 @@ __global__ void __launch_bounds__(256) k_tile_popc(const uint32_t *__restrict__ 
 }
 
 // Exclusive scan of the tile counts and the grand total: one CTA of 1024
-// threads, each taking 8 consecutive counts per round (8192 tiles a round).
-constexpr uint32_t kScanItems = 8;
+// threads, 32 counts per thread per round (32768 tiles a round, the 2^26 words
+// of [0, 2^32) in one).  A round stages its counts in shared memory with a
+// coalesced load, count i at i + i / 32 (so that the 32 consecutive counts a
+// thread scans lie in 32 different banks), scans them there, and writes the
+// offsets with a coalesced store.  Within a round the prefixes fit 32 bits: a
+// tile holds at most 65536 set bits.
+constexpr uint32_t kScanItems = 32;
+constexpr uint32_t kScanThreads = 1024;
+constexpr uint32_t kScanRound = kScanThreads * kScanItems;
+constexpr uint32_t kScanSmemBytes = (kScanRound + kScanRound / 32) * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t *tile_counts, uint64_t *tile_offsets,
-                                                    uint64_t ntiles, unsigned long long *total) {
-    __shared__ unsigned long long s_warp[32];
+__device__ __forceinline__ uint32_t scan_slot(uint32_t i) { return i + (i >> 5); }
+
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan(const uint32_t *tile_counts, uint64_t *tile_offsets,
+                                                            uint64_t ntiles, unsigned long long *total) {
+    extern __shared__ uint32_t s_cnt[];  // kScanRound counts, padded
+    __shared__ uint32_t s_warp[32];
     __shared__ unsigned long long s_run;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_run = 0;
-    __syncthreads();
-    for (uint64_t base = 0; base < ntiles; base += (uint64_t)blockDim.x * kScanItems) {
-        const uint64_t t0 = base + (uint64_t)threadIdx.x * kScanItems;
-        uint32_t v[kScanItems];
-        unsigned long long sum = 0;
-#pragma unroll
-        for (uint32_t i = 0; i < kScanItems; ++i) {
-            v[i] = t0 + i < ntiles ? tile_counts[t0 + i] : 0u;
-            sum += v[i];
-        }
-        unsigned long long x = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
+    for (uint64_t base = 0; base < ntiles; base += kScanRound) {
+#pragma unroll 8
+        for (uint32_t i = threadIdx.x; i < kScanRound; i += kScanThreads)  // 8 loads in flight per thread
+            s_cnt[scan_slot(i)] = base + i < ntiles ? tile_counts[base + i] : 0u;
         __syncthreads();
-        unsigned long long wbase = 0, all = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            if (w < warp) wbase += s_warp[w];
-            all += s_warp[w];
+        const uint32_t t0 = threadIdx.x * kScanItems;
+        uint32_t sum = 0;
+#pragma unroll 8
+        for (uint32_t k = 0; k < kScanItems; ++k) sum += s_cnt[scan_slot(t0 + k)];
+        const uint32_t incl = warp_inclusive_scan_u32(sum, lane);
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        uint32_t wbase = 0, all = 0;
+        for (int w = 0; w < (int)(kScanThreads / 32); ++w) {
+            const uint32_t x = s_warp[w];
+            if (w < warp) wbase += x;
+            all += x;
         }
-        unsigned long long run = s_run + wbase + x - sum;
-#pragma unroll
-        for (uint32_t i = 0; i < kScanItems; ++i) {
-            if (t0 + i < ntiles) tile_offsets[t0 + i] = run;
-            run += v[i];
+        uint32_t run = wbase + incl - sum;  // exclusive prefix of this thread's first count
+#pragma unroll 8
+        for (uint32_t k = 0; k < kScanItems; ++k) {
+            const uint32_t slot = scan_slot(t0 + k), c = s_cnt[slot];
+            s_cnt[slot] = run;
+            run += c;
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_run += all;
-        __syncthreads();
+        const unsigned long long r0 = s_run;
+        for (uint32_t i = threadIdx.x; i < kScanRound && base + i < ntiles; i += kScanThreads)
+            tile_offsets[base + i] = r0 + s_cnt[scan_slot(i)];
+        __syncthreads();  // every thread has read s_run and s_cnt
+        if (threadIdx.x == 0) s_run = r0 + all;
     }
+    __syncthreads();
     if (threadIdx.x == 0) *total = s_run;
 }
 
@@ -203,7 +214,10 @@ cudaError_t launch_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *
 
 cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint64_t ntiles,
                              unsigned long long *total, cudaStream_t stream) {
-    k_tile_scan<<<1, 1024, 0, stream>>>(tile_counts, tile_offsets, ntiles, total);
+    // 132 KiB of counts: above the default 48 KiB (the attribute belongs to the current device)
+    cudaError_t e = cudaFuncSetAttribute(k_tile_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmemBytes);
+    if (e != cudaSuccess) return e;
+    k_tile_scan<<<1, kScanThreads, kScanSmemBytes, stream>>>(tile_counts, tile_offsets, ntiles, total);
     return cudaGetLastError();
 }
 
