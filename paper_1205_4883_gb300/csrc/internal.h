@@ -177,6 +177,12 @@ cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream, uint64_t s
 // out[0] = 2 - sub if *total + 1 <= cap.
 cudaError_t launch_put_two_if_fits(void *out, int out64, const unsigned long long *total, uint64_t cap,
                                    cudaStream_t stream, uint64_t sub = 0);
+// A launch block of at most kUploadMaxBytes (a multiple of 8), copied from host
+// memory into the kernel's parameters at the call, written to dst; acc[0 .. acc_n)
+// zeroed.  The host block may be rewritten as soon as this returns.
+constexpr size_t kUploadMaxBytes = 2048;
+cudaError_t launch_upload(void *dst, const void *src, size_t bytes, unsigned long long *acc, size_t acc_n,
+                          cudaStream_t stream);
 // *out = *count, or UINT64_MAX when *overflow is set.
 cudaError_t launch_finalize_count(const unsigned long long *count, const unsigned *overflow, uint64_t *out,
                                   cudaStream_t stream);

@@ -156,12 +156,29 @@ int block_wait(sieve_ctx *ctx, LaunchBuffers &lb) {
     return SIEVE_OK;
 }
 
-// After the copies of lb's pinned block: mark it consumed (not inside a graph
-// capture, whose copies run at replay, after which the caller synchronises).
-static int mark_consumed(sieve_ctx *ctx, LaunchBuffers &lb, cudaStream_t stream) {
+// The first bytes of lb's pinned block to the device and its accumulators
+// [0, acc_n) zeroed.  Outside a graph capture a block of at most kUploadMaxBytes
+// goes as a kernel parameter (one launch instead of a copy and a memset; the
+// host block is free again at once).  Otherwise it is copied, and an event marks
+// when the copy has run (not inside a capture, whose copies run at replay, after
+// which the caller synchronises).  extra: the Miller-Rabin lists (n_list
+// entries) are copied too.
+static int upload_block(sieve_ctx *ctx, LaunchBuffers &lb, size_t bytes, size_t acc_n, size_t n_list,
+                        cudaStream_t stream) {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(stream, &st));
-    if (st == cudaStreamCaptureStatusNone && lb.consumed) CK(cudaEventRecord(lb.consumed, stream));
+    const bool capturing = st != cudaStreamCaptureStatusNone;
+    if (!capturing && !n_list && bytes <= kUploadMaxBytes) {
+        CK(launch_upload(lb.d_block, lb.h_block, bytes, lb.d_acc, acc_n, stream));
+        return SIEVE_OK;
+    }
+    CK(cudaMemcpyAsync(lb.d_block, lb.h_block, bytes, cudaMemcpyHostToDevice, stream));
+    if (n_list) {
+        CK(cudaMemcpyAsync(lb.d_mr(), lb.h_mr(), n_list * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(lb.d_mrw(), lb.h_mrw(), (n_list + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+    }
+    if (!capturing && lb.consumed) CK(cudaEventRecord(lb.consumed, stream));
+    CK(cudaMemsetAsync(lb.d_acc, 0, acc_n * sizeof(unsigned long long), stream));
     return SIEVE_OK;
 }
 
@@ -412,14 +429,8 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
 // n_list: entries of the Miller-Rabin list to copy.
 int enqueue_launch(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, int mode, LaunchBuffers &lb, size_t m,
                    int grid, int mr_grid, size_t n_list) {
-    CK(cudaMemcpyAsync(lb.d_block, lb.h_block, kLaunchHeader + m * sizeof(RangeDesc), cudaMemcpyHostToDevice, stream));
-    if (n_list) {
-        CK(cudaMemcpyAsync(lb.d_mr(), lb.h_mr(), n_list * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(lb.d_mrw(), lb.h_mrw(), (n_list + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
-    }
-    int rc = mark_consumed(ctx, lb, stream);
+    int rc = upload_block(ctx, lb, kLaunchHeader + m * sizeof(RangeDesc), m + 2, n_list, stream);
     if (rc) return rc;
-    CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
     const SieveLaunch *d = reinterpret_cast<const SieveLaunch *>(lb.d_block);
     const uint32_t smem = reinterpret_cast<const SieveLaunch *>(lb.h_block)->seg_bytes;  // the largest segment
     if (grid > 0) CK(launch_sieve(mode, d, grid, prm.threads, smem, stream));
@@ -538,10 +549,8 @@ int prepare_launch210(sieve_ctx *ctx, const Params &prm, LaunchBuffers &lb, size
 
 // Block copy, accumulator clear and the mod-210 sieve over `grid` CTAs.
 int enqueue_launch210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, LaunchBuffers &lb, size_t m, int grid) {
-    CK(cudaMemcpyAsync(lb.d_block, lb.h_block, kLaunchHeader + m * sizeof(RangeDesc), cudaMemcpyHostToDevice, stream));
-    int rc = mark_consumed(ctx, lb, stream);
+    int rc = upload_block(ctx, lb, kLaunchHeader + m * sizeof(RangeDesc), m + 2, 0, stream);
     if (rc) return rc;
-    CK(cudaMemsetAsync(lb.d_acc, 0, (m + 2) * sizeof(unsigned long long), stream));
     const uint32_t smem = (reinterpret_cast<const SieveLaunch *>(lb.h_block)->seg_bytes + 15) & ~15u;
     if (grid > 0)
         CK(launch_sieve210(reinterpret_cast<const SieveLaunch *>(lb.d_block), ctx->d_tab210, ctx->d_tile210,

@@ -21,6 +21,8 @@
 
 #include "internal.h"
 
+#include <cstring>
+
 namespace gbs {
 namespace {
 
@@ -957,6 +959,29 @@ cudaError_t launch_magic(const uint32_t *primes, uint64_t *magic, uint64_t n, cu
 cudaError_t launch_finalize_count(const unsigned long long *count, const unsigned *overflow, uint64_t *out,
                                   cudaStream_t stream) {
     k_finalize_count<<<1, 1, 0, stream>>>(count, overflow, out);
+    return cudaGetLastError();
+}
+
+namespace {
+struct UploadBlock {
+    uint64_t w[kUploadMaxBytes / 8];
+};
+
+// The launch block, passed by value, written to device memory, and the
+// accumulators zeroed: one launch in place of a host-to-device copy and a memset.
+__global__ void k_upload(const __grid_constant__ UploadBlock blk, uint32_t words, uint64_t *dst,
+                         unsigned long long *acc, uint32_t acc_n) {
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = blk.w[i];
+    for (uint32_t i = threadIdx.x; i < acc_n; i += blockDim.x) acc[i] = 0;
+}
+}  // namespace
+
+cudaError_t launch_upload(void *dst, const void *src, size_t bytes, unsigned long long *acc, size_t acc_n,
+                          cudaStream_t stream) {
+    if (bytes > kUploadMaxBytes || bytes % 8 || acc_n > 0xffffffffu) return cudaErrorInvalidValue;
+    UploadBlock blk;
+    std::memcpy(blk.w, src, bytes);
+    k_upload<<<1, 128, 0, stream>>>(blk, (uint32_t)(bytes / 8), static_cast<uint64_t *>(dst), acc, (uint32_t)acc_n);
     return cudaGetLastError();
 }
 
