@@ -168,15 +168,14 @@ cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint
 // *n = (*total, or 0 if total is null) + add: the device-side count of the asynchronous compaction.
 cudaError_t launch_store_count(const unsigned long long *total, uint32_t add, uint64_t *n, cudaStream_t stream);
 // With total != null, writes only if *total + base_index <= cap (else nothing).
+// base_index = 1 also puts `two` at out[0]; n_out (if set) = *total + base_index.
 cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets,
                         uint64_t ntiles, uint64_t o0, uint32_t base_index, void *out,
                         int out64, int num_sms, cudaStream_t stream,
-                        const unsigned long long *total = nullptr, uint64_t cap = 0);
+                        const unsigned long long *total = nullptr, uint64_t cap = 0, uint64_t two = 2,
+                        uint64_t *n_out = nullptr);
 // out[0] = 2 - sub (sub: the value base a list is written relative to, 0 for primes).
 cudaError_t launch_put_two(void *out, int out64, cudaStream_t stream, uint64_t sub = 0);
-// out[0] = 2 - sub if *total + 1 <= cap.
-cudaError_t launch_put_two_if_fits(void *out, int out64, const unsigned long long *total, uint64_t cap,
-                                   cudaStream_t stream, uint64_t sub = 0);
 // A launch block of at most kUploadMaxBytes (a multiple of 8), copied from host
 // memory into the kernel's parameters at the call, written to dst; acc[0 .. acc_n)
 // zeroed.  The host block may be rewritten as soon as this returns.

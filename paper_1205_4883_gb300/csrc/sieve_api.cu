@@ -579,12 +579,11 @@ int compact_async(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const
     if (ntiles) {
         CK(launch_tile_popc(bitmap_dev, nwords, cs.counts, ntiles, ctx->num_sms * 8, stream));
         CK(launch_tile_scan(cs.counts, cs.offsets, ntiles, cs.d_total, stream));
-        if (out_dev) {
-            if (two) CK(launch_put_two_if_fits(out_dev, out64, cs.d_total, cap, stream));
+        if (out_dev)  // also the prime 2 and the count
             CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, lo | 1, two, out_dev, out64, ctx->num_sms,
-                           stream, cs.d_total, cap));
-        }
-        CK(launch_store_count(cs.d_total, two, n_dev, stream));
+                           stream, cs.d_total, cap, 2, n_dev));
+        else
+            CK(launch_store_count(cs.d_total, two, n_dev, stream));
         return SIEVE_OK;
     }
     // no odd integer in the range: the list is [2] or empty
@@ -609,9 +608,8 @@ int compact_with(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const 
         CK(launch_tile_popc(bitmap_dev, nwords, cs.counts, ntiles, grid, stream));
         CK(launch_tile_scan(cs.counts, cs.offsets, ntiles, cs.d_total, stream));
         if (out_dev) {
-            if (two) CK(launch_put_two_if_fits(out_dev, out64, cs.d_total, cap, stream, sub));
             CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, (lo | 1) - sub, two, out_dev, out64,
-                           ctx->num_sms, stream, cs.d_total, cap));
+                           ctx->num_sms, stream, cs.d_total, cap, 2 - sub));
         }
         CK(cudaMemcpyAsync(cs.h_total, cs.d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));

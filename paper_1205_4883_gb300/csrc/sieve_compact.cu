@@ -144,13 +144,20 @@ __device__ __forceinline__ void emit_lane_desc(const uint32_t (&w)[8], V v, T *p
 // most one tile ahead of another.  With total != null the list is written only
 // if it fits: *total (from k_tile_scan) + base_index <= cap; otherwise the
 // kernel writes nothing, so the host can launch it before it has read the total.
+// base_index = 1 puts `two` (the prime 2, less the value base) at out[0]; n_out,
+// if set, receives *total + base_index, the list's length.
 template <typename T>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ bitmap, uint64_t nwords,
                                               const uint64_t *__restrict__ tile_offsets, uint64_t ntiles,
                                               uint64_t o0, uint32_t base_index, T *__restrict__ out,
-                                              const unsigned long long *total, uint64_t cap) {
+                                              const unsigned long long *total, uint64_t cap, T two,
+                                              uint64_t *n_out) {
     __shared__ uint32_t s_warp[2][8];
     extern __shared__ __align__(16) unsigned char s_dyn[];  // 8 stages of kEmitStage entries
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (n_out) *n_out = (total ? *total : 0ull) + base_index;
+        if (base_index && (!total || *total + base_index <= cap)) out[0] = two;
+    }
     if (total && *total + base_index > cap) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool vec = (reinterpret_cast<uintptr_t>(bitmap) & 15u) == 0;
@@ -246,7 +253,7 @@ cudaError_t emit_ctas_per_sm(int *per_sm) {
 
 cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t *tile_offsets, uint64_t ntiles,
                         uint64_t o0, uint32_t base_index, void *out, int out64, int num_sms, cudaStream_t stream,
-                        const unsigned long long *total, uint64_t cap) {
+                        const unsigned long long *total, uint64_t cap, uint64_t two, uint64_t *n_out) {
     if (ntiles == 0) return cudaSuccess;
     int per_sm = 0;
     cudaError_t e = out64 ? emit_ctas_per_sm<uint64_t>(&per_sm) : emit_ctas_per_sm<uint32_t>(&per_sm);
@@ -256,11 +263,11 @@ cudaError_t launch_emit(const uint32_t *bitmap, uint64_t nwords, const uint64_t 
     if (out64) {
         const int smem = 8 * kEmitStage * sizeof(uint64_t);  // 64 KiB: above the default 48 KiB
         k_emit<uint64_t><<<g, 256, smem, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
-                                                   static_cast<uint64_t *>(out), total, cap);
+                                                   static_cast<uint64_t *>(out), total, cap, two, n_out);
     } else {
         const int smem = 8 * kEmitStage * sizeof(uint32_t);
         k_emit<uint32_t><<<g, 256, smem, stream>>>(bitmap, nwords, tile_offsets, ntiles, o0, base_index,
-                                                   static_cast<uint32_t *>(out), total, cap);
+                                                   static_cast<uint32_t *>(out), total, cap, (uint32_t)two, n_out);
     }
     return cudaGetLastError();
 }
@@ -273,24 +280,6 @@ __global__ void k_store_count(const unsigned long long *total, uint32_t add, uin
 
 cudaError_t launch_store_count(const unsigned long long *total, uint32_t add, uint64_t *n, cudaStream_t stream) {
     k_store_count<<<1, 1, 0, stream>>>(total, add, n);
-    return cudaGetLastError();
-}
-
-namespace {
-// out[0] = two (the prime 2, less the value base) when the list fits: *total + 1 <= cap.
-template <typename T>
-__global__ void k_put_two_if_fits(T *out, const unsigned long long *total, uint64_t cap, T two) {
-    if (*total + 1 <= cap) out[0] = two;
-}
-}  // namespace
-
-cudaError_t launch_put_two_if_fits(void *out, int out64, const unsigned long long *total, uint64_t cap,
-                                   cudaStream_t stream, uint64_t sub) {
-    if (out64)
-        k_put_two_if_fits<uint64_t><<<1, 1, 0, stream>>>(static_cast<uint64_t *>(out), total, cap, 2 - sub);
-    else
-        k_put_two_if_fits<uint32_t><<<1, 1, 0, stream>>>(static_cast<uint32_t *>(out), total, cap,
-                                                         (uint32_t)(2 - sub));
     return cudaGetLastError();
 }
 
