@@ -269,10 +269,18 @@ int prepare_launch(sieve_ctx *ctx, const Params &prm, int mode, LaunchBuffers &l
     // Per range: per-phase sub-progressions for primes below S / 3 (about three hits
     // per progression in a full segment; measured best on pi(10^12) among S / 8 ..
     // S / 2.8), and bucket lists from the bucket limit on (never below the walk tier).
+    // A range of one segment shorter than S takes a third of its own length: above
+    // it a prime has few hits there, and the walk visits only those, while the
+    // per-phase tier sets up every class of every prime for each segment.
     uint32_t mid_lo = 0xffffffffu, mid_hi = small_end, bfirst = 0xffffffffu;
     for (size_t i = 0; i < m; ++i) {
         const uint32_t ml = ro && ro[i].mid_limit ? ro[i].mid_limit : prm.mid_limit;
-        const uint32_t mid_lim = ml ? ml : std::max<uint32_t>(rd[i].seg_bytes / 3, 23);
+        uint32_t len = rd[i].seg_bytes;
+        if (rd[i].nseg == 1) {  // wheel bytes from the grid origin to hi
+            const int64_t ints = (int64_t)rd[i].hi - 30 * rd[i].Bbase;
+            len = (uint32_t)std::min<int64_t>(len, std::max<int64_t>((ints + 29) / 30, 1));
+        }
+        const uint32_t mid_lim = ml ? ml : std::max<uint32_t>(len / 3, 23);
         rd[i].mid_end = std::max(small_end, first_at_least(h, mid_lim));
         const uint64_t bl = ro && ro[i].bucket_limit ? ro[i].bucket_limit : prm.bucket_limit;
         const uint32_t bf = std::max(first_at_least(h, bl ? bl : rd[i].seg_bytes), rd[i].mid_end);
