@@ -168,6 +168,32 @@ def test_list_results_beyond_the_pinned_arena(sv):
             assert srv.release(t) == gb.SIEVE_OK
 
 
+def test_offset_results_beyond_the_pinned_arena(sv):
+    # six offset lists of ~48M primes (~190 MB each, 1.15 GB in all) held at once: the last
+    # ones overflow the 1 GiB pinned arena onto the heap (bounce buffer, 4-byte elements)
+    ranges = [(10**9 * k + 7, 10**9 * (k + 1) + 7) for k in range(1, 7)]
+    with gb.Server(sv, max_device_bytes=6 << 30) as srv:
+        tickets = []
+        for lo, hi in ranges:
+            rc, t = srv.submit(lo, hi, gb.SIEVE_REQ_LIST_OFFSETS)
+            assert rc == gb.SIEVE_OK
+            tickets.append(t)
+        results = []
+        for t in tickets:  # every result held before any is released: they overflow the arena
+            rc, res = srv.poll(t, timeout_us=120_000_000)
+            assert rc == gb.SIEVE_OK and res["status"] == gb.SIEVE_OK
+            results.append(res)
+        assert 4 * sum(r["count"] for r in results) > 1 << 30
+        for (lo, hi), res in zip(ranges, results):
+            want = sv.primes(lo, hi, dtype64=True).cpu().numpy().view(np.uint64)
+            assert res["count"] == len(want)
+            assert np.array_equal(res["offsets"].astype(np.uint64) + np.uint64(lo), want), (lo, hi)
+        for t in tickets:
+            assert srv.release(t) == gb.SIEVE_OK
+    lo, hi = ranges[-1]
+    assert len(want) == oracle.count(lo, hi)
+
+
 def test_completion_queue_reports_each_request_once(sv):
     # sieve_server_wait_any: every admitted request is reported exactly once, whether or
     # not it was polled first, and results read after it are the requests' own
