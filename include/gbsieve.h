@@ -135,9 +135,14 @@ int sieve_compact(sieve_ctx *ctx, const uint32_t *bitmap_dev, uint64_t lo,
  * sieve_bitmap_dev: *count_dev (required) = the number of primes in [lo, hi),
  *   or UINT64_MAX if a bucket list overflowed or a device-side wait gave up;
  *   the bitmap is then not valid (the synchronous call retries instead).
- * sieve_compact_dev: *n_dev = the number of primes in [lo, hi).  The list is
- *   written only if it fits (*n_dev <= cap); otherwise nothing is written and
- *   the caller sees *n_dev > cap after synchronising.  Requires hi <= 2^32.
+ * sieve_compact_dev: *n_dev = the number of primes in [lo, hi), or UINT64_MAX
+ *   if the compaction's bounded wait for another tile's offset gave up (then
+ *   the list is not valid; not seen in normal runs).  The list is written in one
+ *   pass (each tile's offset found by decoupled look-back, no separate counting
+ *   pass), so it is not known to fit before it is written: the first
+ *   min(*n_dev, cap) primes are written, and *n_dev > cap after synchronising
+ *   means the list was truncated.  cap = 0 with out_dev = NULL is the size query.
+ *   Requires hi <= 2^32.
  */
 int sieve_bitmap_dev(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *out_dev,
                      size_t out_words, uint64_t *count_dev);

@@ -73,6 +73,7 @@ struct CompactScratch {
     uint64_t *offsets = nullptr;
     unsigned long long *d_total = nullptr;
     unsigned long long *h_total = nullptr;  // pinned
+    unsigned long long *status = nullptr;   // cap + 1 words: the single-pass compaction's tile states
     size_t cap = 0;                          // tiles
 };
 

@@ -165,6 +165,12 @@ cudaError_t launch_tile_popc(const uint32_t *bitmap, uint64_t nwords, uint32_t *
                              uint64_t ntiles, int grid, cudaStream_t stream);
 cudaError_t launch_tile_scan(uint32_t *tile_counts, uint64_t *tile_offsets, uint64_t ntiles,
                              unsigned long long *total, cudaStream_t stream);
+// Single-pass compaction (tile offsets by decoupled look-back, no popcount pass or
+// scan): the first min(n, cap) values written, n (or UINT64_MAX if a look-back gave
+// up) to *n_out.  status: ntiles + 1 words, zeroed before the launch.
+cudaError_t launch_emit_onepass(const uint32_t *bitmap, uint64_t nwords, uint64_t ntiles, uint64_t o0,
+                                uint32_t base_index, void *out, int out64, int num_sms, cudaStream_t stream, uint64_t cap,
+                                uint64_t two, unsigned long long *status, uint64_t *n_out);
 // *n = (*total, or 0 if total is null) + add: the device-side count of the asynchronous compaction.
 cudaError_t launch_store_count(const unsigned long long *total, uint32_t add, uint64_t *n, cudaStream_t stream);
 // With total != null, writes only if *total + base_index <= cap (else nothing).

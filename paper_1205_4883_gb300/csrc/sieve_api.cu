@@ -191,10 +191,13 @@ int alloc_compact_scratch(sieve_ctx *ctx, CompactScratch &cs, size_t tiles) {
     if (tiles <= cs.cap) return SIEVE_OK;
     dev_free(ctx, cs.counts, cs.cap);
     dev_free(ctx, cs.offsets, cs.cap);
+    dev_free(ctx, cs.status, cs.cap + 1);
     cs.cap = 0;
     int rc = dev_alloc(ctx, &cs.counts, tiles);
     if (rc) return rc;
     rc = dev_alloc(ctx, &cs.offsets, tiles);
+    if (rc) return rc;
+    rc = dev_alloc(ctx, &cs.status, tiles + 1);
     if (rc) return rc;
     cs.cap = tiles;
     return SIEVE_OK;
@@ -203,6 +206,7 @@ int alloc_compact_scratch(sieve_ctx *ctx, CompactScratch &cs, size_t tiles) {
 void free_compact_scratch(sieve_ctx *ctx, CompactScratch &cs) {
     dev_free(ctx, cs.counts, cs.cap);
     dev_free(ctx, cs.offsets, cs.cap);
+    dev_free(ctx, cs.status, cs.cap + 1);
     dev_free(ctx, cs.d_total, 1);
     if (cs.h_total) cudaFreeHost(cs.h_total);
     cs = CompactScratch();
@@ -575,8 +579,10 @@ int launch_ranges210(sieve_ctx *ctx, cudaStream_t stream, const Params &prm, Lau
     return enqueue_launch210(ctx, stream, prm, lb, m, (int)std::min<uint64_t>(grid, items));
 }
 
-// The same kernels as compact_with without the host read of the total: the
-// count goes to the device integer *n_dev and nothing waits for the stream.
+// Compaction without the host read of the total: the count goes to the device
+// integer *n_dev and nothing waits for the stream.  A list is written in one pass
+// (tile offsets by decoupled look-back), truncated at cap; a size query (no
+// output) takes the popcount and scan kernels.
 int compact_async(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const uint32_t *bitmap_dev, uint64_t lo,
                   uint64_t hi, void *out_dev, size_t cap, uint64_t *n_dev, int out64) {
     const uint64_t nwords = bitmap_words_of(lo, hi);
@@ -585,13 +591,15 @@ int compact_async(sieve_ctx *ctx, cudaStream_t stream, CompactScratch &cs, const
     int rc = alloc_compact_scratch(ctx, cs, ntiles);
     if (rc) return rc;
     if (ntiles) {
-        CK(launch_tile_popc(bitmap_dev, nwords, cs.counts, ntiles, ctx->num_sms * 8, stream));
-        CK(launch_tile_scan(cs.counts, cs.offsets, ntiles, cs.d_total, stream));
-        if (out_dev)  // also the prime 2 and the count
-            CK(launch_emit(bitmap_dev, nwords, cs.offsets, ntiles, lo | 1, two, out_dev, out64, ctx->num_sms,
-                           stream, cs.d_total, cap, 2, n_dev));
-        else
+        if (out_dev) {  // also the prime 2 and the count
+            CK(cudaMemsetAsync(cs.status, 0, (ntiles + 1) * sizeof(unsigned long long), stream));
+            CK(launch_emit_onepass(bitmap_dev, nwords, ntiles, lo | 1, two, out_dev, out64, ctx->num_sms, stream, cap,
+                                   2, cs.status, n_dev));
+        } else {
+            CK(launch_tile_popc(bitmap_dev, nwords, cs.counts, ntiles, ctx->num_sms * 8, stream));
+            CK(launch_tile_scan(cs.counts, cs.offsets, ntiles, cs.d_total, stream));
             CK(launch_store_count(cs.d_total, two, n_dev, stream));
+        }
         return SIEVE_OK;
     }
     // no odd integer in the range: the list is [2] or empty

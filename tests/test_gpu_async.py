@@ -84,20 +84,25 @@ def test_back_to_back_async_calls_behind_a_long_launch(sv):
     assert np.array_equal(bm.cpu().numpy().view(np.uint32), oracle.bitmap(lo, hi))
 
 
-def test_compact_dev_below_capacity_writes_nothing(sv):
+def test_compact_dev_below_capacity_truncates(sv):
+    # one pass: a list that does not fit is written up to cap (the prime 2 included),
+    # nothing beyond it; cap = 0 without an output is the size query
     lo, hi = 0, 10**6
+    want = oracle.primes(lo, hi)
     nw = gb.sieve_bitmap_words(lo, hi)
     bm = torch.zeros(nw, dtype=torch.int32, device="cuda")
     n = torch.full((1,), -1, dtype=torch.int64, device="cuda")
     _sync()
     gb.sieve_bitmap_dev(sv.ctx, lo, hi, bm, n)
-    for cap in (0, 1, PI[10**6] - 1):
+    for cap in (0, 1, 2, 2047, 40_000, PI[10**6] - 1):
         lst = torch.full((PI[10**6] + 1,), -3, dtype=torch.int32, device="cuda")
         _sync()
         gb.sieve_compact_dev(sv.ctx, bm, lo, hi, lst if cap else None, n, cap=cap)
         _sync()
         assert int(n.item()) == PI[10**6]
-        assert (lst.cpu() == -3).all(), cap
+        got = lst.cpu().numpy()
+        assert np.array_equal(got[:cap].view(np.uint32).astype(np.uint64), want[:cap]), cap
+        assert (got[cap:] == -3).all(), cap
     lst = torch.full((PI[10**6],), -3, dtype=torch.int32, device="cuda")
     _sync()
     gb.sieve_compact_dev(sv.ctx, bm, lo, hi, lst, n)
