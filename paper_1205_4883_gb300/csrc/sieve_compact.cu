@@ -262,17 +262,21 @@ constexpr uint32_t kLookbackPolls = 1u << 20;
 // that does not fit is truncated).  base_index = 1 puts `two` at out[0]; the last
 // tile writes the list's length (or UINT64_MAX if a look-back gave up) to *n_out.
 // status: ntiles + 1 words, zeroed before the launch.
+// CTA of the single-pass compaction: eight warps that emit (as in k_emit) and
+// one that publishes the tile's count and looks back for its offset meanwhile.
+constexpr uint32_t kOnePassThreads = 288;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_emit_onepass(const uint32_t *__restrict__ bitmap, uint64_t nwords,
+__global__ void __launch_bounds__(kOnePassThreads) k_emit_onepass(const uint32_t *__restrict__ bitmap, uint64_t nwords,
                                                       uint64_t ntiles, uint64_t o0, uint32_t base_index,
                                                       T *__restrict__ out, uint64_t cap, T two,
                                                       unsigned long long *status, uint64_t *n_out) {
     __shared__ uint32_t s_warp[2][8];
     __shared__ unsigned long long s_tile, s_prefix;
     extern __shared__ __align__(16) unsigned char s_dyn[];  // 8 stages of kEmitStage entries
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;  // warp 8 looks back
     const bool vec = (reinterpret_cast<uintptr_t>(bitmap) & 15u) == 0;
-    T *const stage = reinterpret_cast<T *>(s_dyn) + (size_t)warp * kEmitStage;
+    T *const stage = reinterpret_cast<T *>(s_dyn) + (size_t)(warp < 8 ? warp : 0) * kEmitStage;
     if (blockIdx.x == 0 && threadIdx.x == 0 && base_index && cap) out[0] = two;
     uint32_t par = 0;
     for (;; par ^= 1u) {
@@ -281,24 +285,27 @@ __global__ void __launch_bounds__(256) k_emit_onepass(const uint32_t *__restrict
         const uint64_t t = s_tile;
         if (t >= ntiles) break;
         const uint64_t w0 = t * kCompactTileWords + 256ull * warp + 8ull * lane;  // this lane's first word
-        uint32_t w[8];
-        if (vec && w0 + 8 <= nwords) {
-            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(bitmap + w0));
-            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(bitmap + w0) + 1);
-            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-            w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-        } else {
+        uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        uint32_t c = 0, incl = 0, n = 0;
+        if (warp < 8) {
+            if (vec && w0 + 8 <= nwords) {
+                const uint4 a = __ldg(reinterpret_cast<const uint4 *>(bitmap + w0));
+                const uint4 b = __ldg(reinterpret_cast<const uint4 *>(bitmap + w0) + 1);
+                w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+                w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+            } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) w[k] = w0 + k < nwords ? __ldg(bitmap + w0 + k) : 0u;
+                for (int k = 0; k < 8; ++k) w[k] = w0 + k < nwords ? __ldg(bitmap + w0 + k) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) c += __popc(w[k]);
+            incl = warp_inclusive_scan_u32(c, lane);
+            n = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane == 0) s_warp[par][warp] = n;
         }
-        uint32_t c = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) c += __popc(w[k]);
-        const uint32_t incl = warp_inclusive_scan_u32(c, lane);
-        const uint32_t n = __shfl_sync(0xffffffffu, incl, 31);
-        if (lane == 0) s_warp[par][warp] = n;
         __syncthreads();
-        if (warp == 0) {  // the look-back, 32 statuses per step
+        const uint64_t v = o0 + 64ull * w0;
+        if (warp == 8) {  // the look-back, 32 statuses per step
             unsigned long long agg = 0;
             for (int i = 0; i < 8; ++i) agg += s_warp[par][i];
             unsigned long long prefix = 0;
@@ -309,21 +316,21 @@ __global__ void __launch_bounds__(256) k_emit_onepass(const uint32_t *__restrict
                 for (int64_t hi_j = (int64_t)t - 1;; hi_j -= 32) {
                     const int64_t j = hi_j - lane;  // lane 0 reads the nearest tile
                     volatile unsigned long long *sj = status + (j >= 0 ? j : 0);
-                    unsigned long long v = 2ull << 62;  // before tile 0: a prefix of 0
-                    if (j >= 0) v = *sj;
-                    for (uint32_t polls = 0; __any_sync(0xffffffffu, (v >> 62) == 0);) {
+                    unsigned long long x0 = 2ull << 62;  // before tile 0: a prefix of 0
+                    if (j >= 0) x0 = *sj;
+                    for (uint32_t polls = 0; __any_sync(0xffffffffu, (x0 >> 62) == 0);) {
                         if (++polls >= kLookbackPolls) break;
                         __nanosleep(64);
-                        if ((v >> 62) == 0) v = *sj;
+                        if ((x0 >> 62) == 0) x0 = *sj;
                     }
-                    const bool bad = (v >> 62) == 0 || v == (kTilePrefix | kTileValue);
+                    const bool bad = (x0 >> 62) == 0 || x0 == (kTilePrefix | kTileValue);
                     if (__any_sync(0xffffffffu, bad)) {  // gave up, or a poisoned prefix
                         poisoned = true;
                         break;
                     }
-                    const uint32_t pm = __ballot_sync(0xffffffffu, (v >> 62) == 2);
+                    const uint32_t pm = __ballot_sync(0xffffffffu, (x0 >> 62) == 2);
                     const int stop = pm ? __ffs(pm) - 1 : 31;  // the nearest prefix, or the whole window
-                    unsigned long long x = lane <= stop ? (v & kTileValue) : 0ull;
+                    unsigned long long x = lane <= stop ? (x0 & kTileValue) : 0ull;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
                     prefix += x;
@@ -338,20 +345,20 @@ __global__ void __launch_bounds__(256) k_emit_onepass(const uint32_t *__restrict
                 s_prefix = poisoned ? ~0ull : prefix;
                 if (t == ntiles - 1 && n_out) *n_out = poisoned ? ~0ull : prefix + agg + base_index;
             }
-        }
-        __syncthreads();
-        const unsigned long long prefix = s_prefix;
-        if (prefix == ~0ull) continue;  // a look-back gave up: this tile writes nothing
-        uint64_t first = base_index + prefix;  // rank of the warp's first prime
-        for (int i = 0; i < warp; ++i) first += s_warp[par][i];
-        const uint64_t v = o0 + 64ull * w0;
-        if (first >= cap) continue;
-        if (n <= kEmitStage) {
+        } else if (n <= kEmitStage) {  // meanwhile the primes into the stages (no offset needed)
             if (sizeof(T) == 4)
                 emit_lane_desc(w, (uint32_t)v, stage + incl);
             else
                 emit_lane_desc(w, v, stage + incl);
-            __syncwarp();
+        }
+        __syncthreads();
+        if (warp == 8) continue;
+        const unsigned long long prefix = s_prefix;
+        if (prefix == ~0ull) continue;  // a look-back gave up: this tile writes nothing
+        uint64_t first = base_index + prefix;  // rank of the warp's first prime
+        for (int i = 0; i < warp; ++i) first += s_warp[par][i];
+        if (first >= cap) continue;
+        if (n <= kEmitStage) {
             const uint32_t lim = first + n <= cap ? n : (uint32_t)(cap - first);
             T *const o = out + first;
             uint32_t i = lane;
@@ -360,7 +367,6 @@ __global__ void __launch_bounds__(256) k_emit_onepass(const uint32_t *__restrict
                 o[i] = a0; o[i + 32] = a1; o[i + 64] = a2; o[i + 96] = a3;
             }
             for (; i < lim; i += 32) o[i] = stage[i];
-            __syncwarp();  // the stage is refilled by the next tile
         } else if (sizeof(T) == 4) {
             emit_lane_desc_capped(w, (uint32_t)v, out, first + incl, cap);
         } else {
@@ -376,13 +382,13 @@ namespace {
 // every call (it belongs to the current device); the occupancy is the same on
 // every device of the one supported architecture.
 template <typename T, typename K>
-cudaError_t ctas_per_sm(K k, std::atomic<int> &cached, int *per_sm) {
+cudaError_t ctas_per_sm(K k, int threads, std::atomic<int> &cached, int *per_sm) {
     const int smem = 8 * kEmitStage * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int n = cached.load(std::memory_order_relaxed);
     if (n <= 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);
         if (e != cudaSuccess) return e;
         if (n <= 0) n = 1;
         cached.store(n, std::memory_order_relaxed);
@@ -394,13 +400,13 @@ cudaError_t ctas_per_sm(K k, std::atomic<int> &cached, int *per_sm) {
 template <typename T>
 cudaError_t emit_ctas_per_sm(int *per_sm) {
     static std::atomic<int> cached{0};
-    return ctas_per_sm<T>(k_emit<T>, cached, per_sm);
+    return ctas_per_sm<T>(k_emit<T>, 256, cached, per_sm);
 }
 
 template <typename T>
 cudaError_t onepass_ctas_per_sm(int *per_sm) {
     static std::atomic<int> cached{0};
-    return ctas_per_sm<T>(k_emit_onepass<T>, cached, per_sm);
+    return ctas_per_sm<T>(k_emit_onepass<T>, (int)kOnePassThreads, cached, per_sm);
 }
 }  // namespace
 
@@ -435,10 +441,10 @@ cudaError_t launch_emit_onepass(const uint32_t *bitmap, uint64_t nwords, uint64_
     const uint64_t grid = (uint64_t)num_sms * per_sm;
     const unsigned g = (unsigned)(ntiles < grid ? ntiles : grid);
     if (out64) {
-        k_emit_onepass<uint64_t><<<g, 256, 8 * kEmitStage * sizeof(uint64_t), stream>>>(
+        k_emit_onepass<uint64_t><<<g, kOnePassThreads, 8 * kEmitStage * sizeof(uint64_t), stream>>>(
             bitmap, nwords, ntiles, o0, base_index, static_cast<uint64_t *>(out), cap, two, status, n_out);
     } else {
-        k_emit_onepass<uint32_t><<<g, 256, 8 * kEmitStage * sizeof(uint32_t), stream>>>(
+        k_emit_onepass<uint32_t><<<g, kOnePassThreads, 8 * kEmitStage * sizeof(uint32_t), stream>>>(
             bitmap, nwords, ntiles, o0, base_index, static_cast<uint32_t *>(out), cap, (uint32_t)two, status, n_out);
     }
     return cudaGetLastError();
